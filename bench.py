@@ -1,0 +1,377 @@
+"""Benchmark of the FKS hot path on one B300 (or N replicas under torchrun).
+
+A step is one pass of the whole path over one batch of synthetic input:
+build of a map over 2^26 distinct uint64 keys (int64 values) followed by a
+lookup batch of 2^26 queries at a 90 % hit rate against it (uniform hits,
+exact non-members for the misses), then the map is released.  Inputs are
+resident in HBM before the timed region (512 MiB per array, far larger than
+the 126 MB L2, so no flush is needed between steps).
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FKS build keys/s & lookups/s (% HBM roofline); served p50/p99 vs per-call"
+N_KEYS = 1 << 26
+N_QUERIES = 1 << 26
+HIT = 0.9
+SEED = 2
+WORKLOAD = "u64 build 2^26 keys + lookup 2^26 queries (90% hits)"
+
+# algorithmic bytes (32-byte sector model) -- see the design notes
+SECTOR = 32
+
+
+def lookup_bytes_per_query(hit_frac: float, nonempty_frac: float) -> float:
+    """needle 8 + descriptor sector + slot sector (hits, and misses that land
+    in a non-empty bucket) + value 8 + found flag 1."""
+    return 8 + SECTOR + SECTOR * (hit_frac + (1 - hit_frac) * nonempty_frac) + 8 + 1
+
+
+def part_build_bytes_per_key(S_over_n: float) -> float:
+    """staged key+value read 16 + descriptor write 8 + slot writes 16 * S/n."""
+    return 16 + 8 + 16 * S_over_n
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def load_traffic():
+    """DRAM bytes per launch from the committed ncu summary, keyed by kernel,
+    with the kernel source digest they were taken at."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.md")
+    out = {}
+    if not os.path.exists(path):
+        return out
+    for line in open(path):
+        m = re.match(r"\|\s*(k_\w+)\s*\|\s*([0-9.eE+]+)\s*\|\s*([0-9a-f]{12})\s*\|", line)
+        if m:
+            out[m.group(1)] = (float(m.group(2)), m.group(3))
+    return out
+
+
+def kernel_digest() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2508_11443_b300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def cpu_sample_run(n: int, nq: int, seed: int):
+    """Oracle build + lookup over a sample of the workload; returns seconds."""
+    import oracle as O
+    from paper_2508_11443_b300 import workloads as W
+    w = W.u64_workload(n, nq, HIT, seed)
+    t0 = time.perf_counter()
+    m = O.build_u64(w.keys, w.vals, seed=seed)
+    out, found = O.lookup_u64(m, w.queries)
+    dt = time.perf_counter() - t0
+    assert m.status == O.OK and np.array_equal(found, w.expect_found)
+    return dt
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    n = min(args.cpu_sample, 1 << 22)
+    times = []
+    for i in range(args.warmup + args.steps):
+        dt = cpu_sample_run(n, n, SEED + 1000 + i)
+        if i >= args.warmup:
+            times.append(dt)
+    per_step = statistics.mean(times)
+    value = 2 * n / per_step
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "keys+lookups/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": per_step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_keys": N_KEYS, "n_queries": N_QUERIES, "hit_rate": HIT,
+                   "sample": f"each step: oracle build of {n} keys + lookup of {n} queries"},
+        "cpu_baseline": {"value": value, "unit": "keys+lookups/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{n} keys built + {n} queries per step, single thread"},
+        "e2e": {"value": value, "unit": "keys+lookups/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fks", choices=["fks", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=1 << 24)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=N_KEYS)
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2508_11443_b300 import build as B
+    from paper_2508_11443_b300 import fks as F
+    from paper_2508_11443_b300 import workloads as W
+
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+    B.build()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    n = args.n
+    nq = n
+    w = W.u64_workload(n, nq, HIT, SEED + rank)
+    keys = torch.from_numpy(w.keys.view(np.int64)).cuda()
+    vals = torch.from_numpy(w.vals).cuda()
+    queries = torch.from_numpy(w.queries.view(np.int64)).cuda()
+    out = torch.empty(nq, dtype=torch.int64, device="cuda")
+    found = torch.empty(nq, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    F.fks_profile_enable(True)
+
+    build_ms, part_ms, lookup_ms, step_ms, nonempty, S = [], [], [], [], [], []
+
+    def step(timed):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        m = F.fks_build_u64(keys, vals, SEED + rank)
+        e1.record(stream)
+        F.fks_lookup_u64(m, queries, out, found, -1)
+        e2.record(stream)
+        if timed:
+            prof = F.fks_last_build_profile()
+            info = F.fks_map_info(m)
+            torch.cuda.synchronize()
+            build_ms.append(e0.elapsed_time(e1))
+            lookup_ms.append(e1.elapsed_time(e2))
+            step_ms.append(e0.elapsed_time(e2))
+            part_ms.append((prof.count_ms, prof.scan_ms, prof.scatter_ms, prof.part_build_ms))
+            nonempty.append(info.nonempty_buckets / info.n)
+            S.append(info.slots / info.n)
+        del m
+
+    for _ in range(args.warmup):
+        step(False)
+    torch.cuda.synchronize()
+    # correctness of the last warm-up lookup
+    f = found.cpu().numpy()
+    o = out.cpu().numpy()
+    assert np.array_equal(f, w.expect_found), "lookup found flags differ from the workload's truth"
+    assert np.array_equal(o, np.where(w.expect_found == 1, w.expect_vals, -1)), "lookup values differ"
+
+    launches0 = F.fks_kernel_launches()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        t_start.record(stream)
+        for _ in range(args.steps):
+            step(True)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    launches = F.fks_kernel_launches() - launches0
+    total_ms = t_start.elapsed_time(t_end)
+    if world > 1:
+        tt = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_per_step = total_ms / args.steps
+    units = (n + nq) * world
+    value = units / (ms_per_step / 1e3)
+
+    # ---- end to end through the C ABI from pinned host memory
+    h_keys = torch.from_numpy(w.keys.view(np.int64)).pin_memory()
+    h_vals = torch.from_numpy(w.vals).pin_memory()
+    h_q = torch.from_numpy(w.queries.view(np.int64)).pin_memory()
+    h_out = torch.empty(nq, dtype=torch.int64).pin_memory()
+    h_found = torch.empty(nq, dtype=torch.uint8).pin_memory()
+
+    def e2e_step():
+        keys.copy_(h_keys, non_blocking=True)
+        vals.copy_(h_vals, non_blocking=True)
+        queries.copy_(h_q, non_blocking=True)
+        m = F.fks_build_u64(keys, vals, SEED + rank)
+        F.fks_lookup_u64(m, queries, out, found, -1)
+        h_out.copy_(out, non_blocking=True)
+        h_found.copy_(found, non_blocking=True)
+        del m
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(3, args.steps // 2)
+    a.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = a.elapsed_time(b) / e2e_steps
+    if world > 1:
+        tt = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+    assert np.array_equal(h_found.numpy(), w.expect_found)
+
+    # ---- roofline of the dominant kernel
+    hbm, peak_kind = load_peaks()
+    med = lambda xs: statistics.median(xs)
+    lk = med(lookup_ms)
+    pb = med([p[3] for p in part_ms])
+    ne = med(nonempty)
+    s_n = med(S)
+    kernels = {
+        "k_lookup_u64": {"ms": lk, "bytes": lookup_bytes_per_query(HIT, ne) * nq,
+                         "model": f"{lookup_bytes_per_query(HIT, ne):.2f} B/query x {nq}"},
+        "k_part_build": {"ms": pb, "bytes": part_build_bytes_per_key(s_n) * n,
+                         "model": f"{part_build_bytes_per_key(s_n):.2f} B/key x {n}"},
+        "k_partition_scatter": {"ms": med([p[2] for p in part_ms]), "bytes": 32.0 * n,
+                                "model": f"32 B/key x {n}"},
+        "k_partition_count": {"ms": med([p[0] for p in part_ms]), "bytes": 8.0 * n,
+                              "model": f"8 B/key x {n}"},
+    }
+    for k, v in kernels.items():
+        v["GBps"] = v["bytes"] / (v["ms"] / 1e3) / 1e9
+        v["frac"] = v["GBps"] / hbm
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    traffic = load_traffic()
+    dig = kernel_digest()
+    tr = None
+    if dom in traffic and traffic[dom][1] == dig:
+        tr = traffic[dom][0]
+    D = kernels[dom]
+    roofline = {"bound": "hbm", "achieved": D["GBps"], "peak": hbm, "unit": "GB/s",
+                "frac": D["frac"], "traffic": tr, "kernel": dom, "peak_source": peak_kind,
+                "bytes_model": D["model"]}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "keys+lookups/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_keys": n, "n_queries": nq, "hit_rate": HIT,
+                   "values": "int64", "seed": SEED, "parallelism": f"replicas{world}",
+                   "l2": "inputs larger than L2 (512 MiB per array), no flush"},
+        "build_keys_per_s": n * world / (med(build_ms) / 1e3),
+        "lookups_per_s": nq * world / (lk / 1e3),
+        "build_ms": med(build_ms), "lookup_ms": lk,
+        "phases_ms": {"count": med([p[0] for p in part_ms]), "scan": med([p[1] for p in part_ms]),
+                      "scatter": med([p[2] for p in part_ms]), "part_build": pb},
+        "S_over_n": s_n, "nonempty_frac": ne,
+        "roofline": roofline,
+        "kernels": {k: {"ms": round(v["ms"], 4), "GBps": round(v["GBps"], 1),
+                        "frac": round(v["frac"], 4), "bytes_model": v["model"]}
+                    for k, v in kernels.items()},
+        "e2e": {"value": units / (e2e_ms / 1e3), "unit": "keys+lookups/s",
+                "h2d_bytes_per_step": int(8 * n + 8 * n + 8 * nq),
+                "d2h_bytes_per_step": int(8 * nq + nq), "ms_per_step": e2e_ms},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(1) as pool:
+            dt = pool.apply(cpu_sample_run, (args.cpu_sample, args.cpu_sample, SEED + 7))
+        line["cpu_baseline"] = {"value": 2 * args.cpu_sample / dt, "unit": "keys+lookups/s",
+                                "cores": 1, "kind": "oracle",
+                                "sample": f"oracle build of {args.cpu_sample} keys + lookup of "
+                                          f"{args.cpu_sample} queries (same generator), "
+                                          f"{os.cpu_count()} host cores available"}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,216 @@
+/*
+ * fks.h -- C ABI of a B300 (sm_103a) library that builds and queries
+ * Fredman-Komlos-Szemeredi two-level, static, collision-free hash maps, the
+ * method of Due, Elsman, Henriksen, "Towards Efficient Hash Maps in
+ * Functional Array Languages" (arXiv 2508.11443).
+ *
+ * The interface follows the paper's `map` module type (Sec. 3.2):
+ *   from_array_nodup  -> fks_build_u64 / fks_build_bytes (duplicates are
+ *                        detected and rejected instead of assumed absent)
+ *   lookup -> opt v   -> fks_lookup_u64 / fks_lookup_bytes (value + found)
+ *   membership        -> a lookup with out_vals == NULL (Sec. 4)
+ * and its key abstraction (Sec. 3.3): fixed-width uint64 keys, or byte-slice
+ * keys (offset, length) into a context array.  The map keeps its own copy of
+ * the context; the needles of a lookup bring theirs (Sec. 3.1).
+ *
+ * Conventions for every call below.
+ *   Pointers: device pointers unless the parameter name starts with h_.
+ *   Streams:  every call is ordered on `stream` (a cudaStream_t; NULL is the
+ *             legacy default stream).  Builds block until the device status
+ *             of the build is known (one stream synchronisation); lookups do
+ *             not block.
+ *   Errors:   every call returns an fks_status and never aborts.  Device-side
+ *             failures come back through a status word, never a trap.
+ *             fks_last_error() gives a one-line description of the last
+ *             failure on the calling thread.
+ *   Ownership: a map owns copies of its keys, values and context; inputs may
+ *             be freed once the build returns.  Handles are freed by
+ *             fks_map_destroy / fks_mapset_destroy.
+ *   Sizes:    1 <= n < 2^30 keys per map; string length < 2^24 bytes;
+ *             context < 2^40 bytes.
+ */
+#ifndef FKS_H_
+#define FKS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+typedef struct CUstream_st* fks_stream_t; /* identical to cudaStream_t */
+
+typedef struct fks_map* fks_map_t;       /* one map                     */
+typedef struct fks_mapset* fks_mapset_t; /* maps built by one batched call */
+
+typedef enum {
+  FKS_OK = 0,
+  FKS_ERR_INVALID_ARG = 1,   /* bad pointer, size, offsets or options          */
+  FKS_ERR_DUPLICATE_KEY = 2, /* two equal keys (equal byte strings)            */
+  FKS_ERR_OUT_OF_MEMORY = 3, /* the allocator returned NULL                    */
+  FKS_ERR_BUILD_FAILED = 4,  /* round_cap level-one rounds failed, no duplicate */
+  FKS_ERR_TIMEOUT = 5,       /* a bounded device wait ran out                  */
+  FKS_ERR_CUDA = 6,          /* a CUDA runtime call failed                     */
+  FKS_ERR_EVICTED = 7        /* serving: the map was evicted                   */
+} fks_status;
+
+typedef enum { FKS_VAL_I32 = 0, FKS_VAL_I64 = 1 } fks_val_type;
+typedef enum { FKS_KEY_U64 = 0, FKS_KEY_BYTES = 1 } fks_key_kind;
+
+/* Device-memory hook.  alloc returns a device pointer aligned to 256 bytes
+ * or NULL; free releases it.  Both are stream-ordered on `stream`.  A NULL
+ * hook (or NULL members) selects cudaMallocAsync / cudaFreeAsync. */
+typedef struct {
+  size_t struct_size; /* sizeof(fks_allocator) */
+  void* (*alloc)(size_t bytes, fks_stream_t stream, void* user);
+  void (*free)(void* ptr, size_t bytes, fks_stream_t stream, void* user);
+  void* user;
+} fks_allocator;
+
+/* Build options; a NULL pointer or a 0 field selects the default. */
+typedef struct {
+  size_t struct_size;        /* sizeof(fks_build_opts)                          */
+  uint32_t bound_factor;     /* level-one redraw when sum s^2 > bound*n (4)     */
+  uint32_t attempt_cap;      /* level-two attempts per bucket and round (4095) */
+  uint32_t round_cap;        /* level-one rounds (32)                           */
+  uint32_t reject_attempts;  /* TEST HOOK: attempts below this count as failed (0) */
+  uint32_t spin_limit;       /* bound of every device wait, in polls (1<<20)     */
+} fks_build_opts;
+
+typedef struct {
+  uint64_t n;             /* keys                                     */
+  uint64_t seed;          /* build seed                               */
+  uint64_t slots;         /* S = sum over buckets of s^2              */
+  uint64_t slot_capacity; /* slots reserved (bound_factor * n)        */
+  uint64_t bytes;         /* device bytes held by the map             */
+  uint64_t attempts_sum;  /* sum of level-two attempt indices         */
+  uint64_t context_bytes; /* strings: bytes of the map's context      */
+  uint32_t round;         /* level-one round that succeeded           */
+  uint32_t max_bucket;    /* largest bucket                           */
+  uint32_t max_attempt;   /* largest level-two attempt index          */
+  uint32_t key_kind;      /* fks_key_kind                             */
+  uint32_t val_type;      /* fks_val_type                             */
+  uint32_t overflow_partitions; /* partitions built through global memory */
+  uint64_t nonempty_buckets;    /* buckets with s > 0                      */
+} fks_map_info_t;
+
+/* Phase timings of the last build on the calling thread (CUDA events on the
+ * build's stream; summed over level-one passes).  Recorded only while
+ * fks_profile_enable(1) is in effect on that thread. */
+typedef struct {
+  float fingerprint_ms; /* string maps: fingerprints of the keys            */
+  float count_ms;       /* level-one hash + keys per partition              */
+  float scan_ms;        /* scan of the partition counts                     */
+  float scatter_ms;     /* keys scattered into partition ranges             */
+  float part_build_ms;  /* per-partition Hist, Presum, make_2, placement    */
+  uint32_t passes;      /* level-one passes run                             */
+} fks_build_profile;
+
+/* ------------------------------------------------------------------ build
+ * fks_build_u64 -- from_array_nodup over uint64 keys (Sec. 2.3 make_1 /
+ * make_2 as a data-parallel construction; Sec. 3.2).
+ *   keys   uint64[n]          distinct keys (device)
+ *   vals   int32[n] or int64[n] per val_type (device)
+ *   seed   selects the hash constants; the table is a pure function of
+ *          (key set, values, seed): the first successful level-one round and,
+ *          per bucket, the first successful level-two attempt are kept.
+ *   opts, alloc  may be NULL.   out  receives the handle (NULL on failure).
+ * Returns FKS_ERR_DUPLICATE_KEY when two keys are equal. */
+fks_status fks_build_u64(const uint64_t* keys, const void* vals, fks_val_type val_type, uint64_t n,
+                         uint64_t seed, const fks_build_opts* opts, const fks_allocator* alloc,
+                         fks_stream_t stream, fks_map_t* out);
+
+/* fks_build_bytes -- the same over byte-string keys in a context (Sec. 3.1,
+ * Sec. 3.3 slices): key i is ctx[offs[i] .. offs[i+1]).
+ *   ctx    uint8[offs[n]] (device), copied into the map
+ *   offs   int64[n+1] non-decreasing, offs[0] >= 0 (device)
+ * Keys are hashed through a 61-bit polynomial fingerprint; equal byte
+ * strings are duplicates, equal fingerprints of different strings make the
+ * build redraw its constants. */
+fks_status fks_build_bytes(const uint8_t* ctx, const int64_t* offs, const void* vals,
+                           fks_val_type val_type, uint64_t n, uint64_t seed,
+                           const fks_build_opts* opts, const fks_allocator* alloc,
+                           fks_stream_t stream, fks_map_t* out);
+
+/* ------------------------------------------------------------------ lookup
+ * fks_lookup_u64 -- lookup -> opt v (Sec. 3.2) with the membership test of
+ * Sec. 2.2: level-one descriptor, then one level-two slot, then a compare.
+ *   q          uint64[nq] needles (device)
+ *   out_vals   int32[nq] / int64[nq] per the map's val_type, or NULL
+ *   out_found  uint8[nq] (1 = present), or NULL
+ *   absent     written to out_vals for needles that are not in the map
+ *              (must fit int32 for int32 maps)
+ * nq == 0 is a no-op.  Does not block. */
+fks_status fks_lookup_u64(fks_map_t map, const uint64_t* q, uint64_t nq, void* out_vals,
+                          uint8_t* out_found, int64_t absent, fks_stream_t stream);
+
+/* fks_lookup_bytes -- needles ctx qctx[qoffs[i] .. qoffs[i+1]) (device),
+ * a context of their own (Sec. 3.1); a hit needs equal fingerprint, length
+ * and bytes. */
+fks_status fks_lookup_bytes(fks_map_t map, const uint8_t* qctx, const int64_t* qoffs, uint64_t nq,
+                            void* out_vals, uint8_t* out_found, int64_t absent,
+                            fks_stream_t stream);
+
+/* ------------------------------------------------------------------ batched
+ * fks_build_batched -- m independent maps over one concatenated input, the
+ * same construction per segment with map-local buckets, so map j's tables
+ * equal those of a per-call build of segment j with seed h_seeds[j].
+ *   keys      uint64[total] for FKS_KEY_U64 (else NULL)
+ *   ctx,offs  for FKS_KEY_BYTES: one context, offs int64[total+1] (else NULL)
+ *   h_seg     int64[m+1] HOST segment offsets, h_seg[0] = 0, every segment
+ *             non-empty
+ *   h_seeds   uint64[m] HOST build seeds
+ *   vals      int32/int64[total] (device)
+ * The status of each map is returned in h_status[m] (may be NULL); the call
+ * returns FKS_OK only if every map was built. */
+fks_status fks_build_batched(fks_key_kind kind, const uint64_t* keys, const uint8_t* ctx,
+                             const int64_t* offs, const int64_t* h_seg, const uint64_t* h_seeds,
+                             uint32_t m, const void* vals, fks_val_type val_type,
+                             const fks_build_opts* opts, const fks_allocator* alloc,
+                             fks_stream_t stream, fks_mapset_t* out, fks_status* h_status);
+
+/* fks_lookup_batched -- (map_id, key) needles against a map set in one
+ * launch.  map_ids uint32[nq] (device); an id >= m is reported absent.
+ * Key kind FKS_KEY_U64 uses q; FKS_KEY_BYTES uses qctx/qoffs. */
+fks_status fks_lookup_batched(fks_mapset_t set, const uint32_t* map_ids, const uint64_t* q,
+                              const uint8_t* qctx, const int64_t* qoffs, uint64_t nq,
+                              void* out_vals, uint8_t* out_found, int64_t absent,
+                              fks_stream_t stream);
+
+/* Number of maps of a set, and a borrowed handle of map j (valid until the
+ * set is destroyed; do not destroy it). */
+uint32_t fks_mapset_size(fks_mapset_t set);
+fks_map_t fks_mapset_get(fks_mapset_t set, uint32_t j);
+
+/* ------------------------------------------------------------------ tables
+ * fks_map_info -- sizes and build statistics (host struct). */
+fks_status fks_map_info(fks_map_t map, fks_map_info_t* h_out);
+
+/* fks_map_export -- copy the tables to host memory (synchronises `stream`):
+ *   h_desc   uint64[n]   bucket descriptors: slot offset (bits 0..31) | s
+ *            (bits 32..51) | level-two attempt (bits 52..63)
+ *   h_slots  S slots: uint64 maps {key, value} (16 B); string maps {fp,
+ *            offset | length << 40, value, 0} (32 B); empty slots hold the
+ *            bucket's lowest occupied slot with value -1
+ *   h_ctx    string maps: the map's context (context_bytes); else ignored
+ * Any pointer may be NULL. */
+fks_status fks_map_export(fks_map_t map, uint64_t* h_desc, void* h_slots, uint8_t* h_ctx,
+                          fks_stream_t stream);
+
+void fks_map_destroy(fks_map_t map);
+void fks_mapset_destroy(fks_mapset_t set);
+
+const char* fks_status_str(fks_status status);
+const char* fks_last_error(void);
+
+/* ------------------------------------------------------------------ metrics */
+void fks_profile_enable(int on);                       /* per calling thread */
+fks_status fks_last_build_profile(fks_build_profile* h_out);
+uint64_t fks_kernel_launches(void); /* kernels launched by this library so far */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FKS_H_ */

@@ -1,0 +1,779 @@
+// fks_api.cu -- host side of the C ABI declared in include/fks.h.
+//
+// A build runs level-one rounds (Sec. 2.3 make_1: a fresh const per round)
+// until every map of the call satisfies the space bound and every bucket
+// found collision-free level-two constants (make_2).  One round of all
+// still-unfinished maps is one "pass" of the device pipeline in
+// fks_build.cu; after each pass the per-map status words are read back (one
+// stream synchronisation) and the maps that must redraw are re-run together.
+// A per-call build is the one-map case of the same code.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "fks.h"
+#include "fks_internal.cuh"
+
+using namespace fks;
+
+// ---------------------------------------------------------------- errors
+static thread_local std::string g_last_error;
+
+static fks_status fail(fks_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+static fks_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(FKS_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+#define FKS_CUDA(call)                                       \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);      \
+  } while (0)
+
+// ---------------------------------------------------------------- metrics
+#include <atomic>
+static std::atomic<uint64_t> g_launches{0};
+void fks::note_launches(uint32_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+static thread_local int g_profile = 0;
+static thread_local fks_build_profile g_last_profile{};
+
+struct ProfileEvents {
+  PassEvents pe{};
+  cudaEvent_t fp0 = nullptr, fp1 = nullptr;
+  bool ok = false;
+  ProfileEvents() {
+    if (!g_profile) return;
+    ok = true;
+    for (auto& e : pe.ev) ok &= cudaEventCreate(&e) == cudaSuccess;
+    ok &= cudaEventCreate(&fp0) == cudaSuccess && cudaEventCreate(&fp1) == cudaSuccess;
+  }
+  ~ProfileEvents() {
+    for (auto& e : pe.ev)
+      if (e) cudaEventDestroy(e);
+    if (fp0) cudaEventDestroy(fp0);
+    if (fp1) cudaEventDestroy(fp1);
+  }
+  // after the pass has been synchronised
+  void accumulate(fks_build_profile* p, bool strings) const {
+    if (!ok) return;
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, pe.ev[0], pe.ev[1]) == cudaSuccess) p->count_ms += ms;
+    if (cudaEventElapsedTime(&ms, pe.ev[1], pe.ev[2]) == cudaSuccess) p->scan_ms += ms;
+    if (cudaEventElapsedTime(&ms, pe.ev[2], pe.ev[3]) == cudaSuccess) p->scatter_ms += ms;
+    if (cudaEventElapsedTime(&ms, pe.ev[3], pe.ev[4]) == cudaSuccess) p->part_build_ms += ms;
+    if (strings && cudaEventElapsedTime(&ms, fp0, fp1) == cudaSuccess) p->fingerprint_ms += ms;
+    p->passes += 1;
+  }
+};
+
+// ---------------------------------------------------------------- device facts
+static int sm_count() {
+  static int sms = 0;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // keep freed blocks in the stream-ordered pool instead of returning them
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    if (sms <= 0) sms = 148;
+  });
+  return sms;
+}
+
+// ---------------------------------------------------------------- memory
+struct Alloc {
+  fks_allocator hook{};
+  bool user = false;
+  explicit Alloc(const fks_allocator* a) {
+    if (a && a->struct_size >= sizeof(fks_allocator) && a->alloc && a->free) {
+      hook = *a;
+      user = true;
+    }
+  }
+  void* get(size_t bytes, cudaStream_t s) const {
+    if (bytes == 0) bytes = 256;
+    bytes = (bytes + 255) & ~size_t(255);
+    if (user) return hook.alloc(bytes, reinterpret_cast<fks_stream_t>(s), hook.user);
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return p;
+  }
+  void put(void* p, size_t bytes, cudaStream_t s) const {
+    if (!p) return;
+    if (bytes == 0) bytes = 256;
+    bytes = (bytes + 255) & ~size_t(255);
+    if (user) hook.free(p, bytes, reinterpret_cast<fks_stream_t>(s), hook.user);
+    else cudaFreeAsync(p, s);
+  }
+};
+
+// Bump carving of one allocation into 256-byte aligned pieces.
+struct Carve {
+  size_t off = 0;
+  template <class T>
+  size_t take(size_t count) {
+    const size_t at = off;
+    off += (count * sizeof(T) + 255) & ~size_t(255);
+    return at;
+  }
+};
+
+// Pinned host staging for small control transfers (per thread).
+struct Pinned {
+  void* p = nullptr;
+  size_t cap = 0;
+  void* get(size_t bytes) {
+    if (bytes > cap) {
+      if (p) cudaFreeHost(p);
+      cap = std::max<size_t>(bytes, 1 << 16);
+      if (cudaMallocHost(&p, cap) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+        cap = 0;
+      }
+    }
+    return p;
+  }
+  ~Pinned() {
+    if (p) cudaFreeHost(p);
+  }
+};
+static thread_local Pinned g_pin_up, g_pin_down;
+
+// ---------------------------------------------------------------- handles
+struct fks_map {
+  fks_key_kind kind = FKS_KEY_U64;
+  fks_val_type vt = FKS_VAL_I64;
+  uint64_t n = 0, seed = 0, S = 0, slot_cap = 0, att_sum = 0, ctx_bytes = 0, bytes = 0;
+  uint64_t nonempty = 0;
+  uint32_t round = 0, max_s = 0, max_att = 0, overflow = 0;
+  HashConsts c1{};
+  uint64_t fpb = 0;
+  uint64_t* desc = nullptr;
+  uint64_t* slots = nullptr;
+  uint8_t* ctx = nullptr;
+  // ownership (null for maps borrowed from a set)
+  void* block = nullptr;
+  size_t block_bytes = 0;
+  Alloc alloc{nullptr};
+};
+
+struct fks_mapset {
+  fks_key_kind kind = FKS_KEY_U64;
+  fks_val_type vt = FKS_VAL_I64;
+  std::vector<fks_map> maps;
+  LookupMap* d_table = nullptr;  // device copy for batched lookups
+  void* block = nullptr;
+  size_t block_bytes = 0;
+  Alloc alloc{nullptr};
+};
+
+static LookupMap lookup_view(const fks_map& m) {
+  LookupMap L;
+  L.desc = m.desc;
+  L.slots = m.slots;
+  L.ctx = m.ctx;
+  L.c1 = m.c1;
+  L.seed = m.seed;
+  L.fpb = m.fpb;
+  L.n = uint32_t(m.n);
+  L.round = m.round;
+  return L;
+}
+
+// ---------------------------------------------------------------- options
+struct Opts {
+  uint32_t bound = 4, attempt_cap = 4095, round_cap = 32, reject = 0, spin = 1u << 20, hold = 0;
+};
+
+static bool read_opts(const fks_build_opts* o, Opts* out) {
+  if (!o) return true;
+  if (o->struct_size < offsetof(fks_build_opts, spin_limit) + sizeof(uint32_t)) return false;
+  if (o->bound_factor) out->bound = o->bound_factor;
+  if (o->attempt_cap) out->attempt_cap = o->attempt_cap;
+  if (o->round_cap) out->round_cap = o->round_cap;
+  out->reject = o->reject_attempts;
+  if (o->spin_limit) out->spin = o->spin_limit;
+  if (out->attempt_cap > 4095 || out->round_cap > 65535 || out->bound < 1 || out->bound > 4)
+    return false;
+  return true;
+}
+
+// test hook (not in the public header): make partition 0 never publish its
+// slot prefix so that the bounded wait of partition 1 runs out.
+static thread_local int g_hold_first_partition = 0;
+extern "C" void fks_test_hold_first_partition(int on) { g_hold_first_partition = on; }
+
+// ---------------------------------------------------------------- the build
+struct BuildIn {
+  fks_key_kind kind;
+  const uint64_t* keys;  // u64 keys (input numbering)
+  const uint8_t* ctx;    // string maps
+  const int64_t* offs;
+  const void* vals;
+  fks_val_type vt;
+  uint32_t m;
+  const int64_t* seg;     // host [m+1]
+  const uint64_t* seeds;  // host [m]
+};
+
+struct SetMem {
+  uint64_t* desc = nullptr;
+  uint64_t* slots = nullptr;
+  uint8_t* ctx = nullptr;
+  std::vector<uint64_t> slot_base;  // per map
+};
+
+static fks_status build_impl(const BuildIn& in, const Opts& o, const Alloc& A, cudaStream_t st,
+                             void** out_block, size_t* out_block_bytes, SetMem* mem,
+                             std::vector<fks_map>* maps_out, std::vector<fks_status>* per_map) {
+  const uint32_t m = in.m;
+  const bool str = in.kind == FKS_KEY_BYTES;
+  const int PW = str ? 2 : 1;
+  const int W = str ? 4 : 2;  // words per slot
+  const uint64_t total = uint64_t(in.seg[m]);
+  uint64_t slot_total = 0;
+  std::vector<uint64_t> slot_base(m);
+  for (uint32_t j = 0; j < m; ++j) {
+    slot_base[j] = slot_total;
+    slot_total += uint64_t(o.bound) * uint64_t(in.seg[j + 1] - in.seg[j]);
+  }
+  // context bytes: offs[total] from the device
+  uint64_t ctx_bytes = 0;
+  if (str) {
+    int64_t last = 0;
+    FKS_CUDA(cudaMemcpyAsync(&last, in.offs + total, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    FKS_CUDA(cudaStreamSynchronize(st));
+    if (last < 0 || last >= (int64_t(1) << 40)) return fail(FKS_ERR_INVALID_ARG, "offsets out of range");
+    ctx_bytes = uint64_t(last);
+  }
+  // the set's own memory: descriptors, slots, context copy
+  Carve cm;
+  const size_t o_desc = cm.take<uint64_t>(total);
+  const size_t o_slots = cm.take<uint64_t>(slot_total * W);
+  const size_t o_ctx = cm.take<uint8_t>(str ? ctx_bytes + 16 : 0);
+  uint8_t* block = static_cast<uint8_t*>(A.get(cm.off, st));
+  if (!block) return fail(FKS_ERR_OUT_OF_MEMORY, "allocation of map tables failed");
+  mem->desc = reinterpret_cast<uint64_t*>(block + o_desc);
+  mem->slots = reinterpret_cast<uint64_t*>(block + o_slots);
+  mem->ctx = str ? block + o_ctx : nullptr;
+  mem->slot_base = slot_base;
+  if (str && ctx_bytes) {
+    cudaError_t e = cudaMemcpyAsync(mem->ctx, in.ctx, ctx_bytes, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) {
+      A.put(block, cm.off, st);
+      return cuda_fail(e, "context copy");
+    }
+  }
+  // scratch for the largest pass (the first one holds every map)
+  uint64_t P_all = 0;
+  for (uint32_t j = 0; j < m; ++j)
+    P_all += (uint64_t(in.seg[j + 1] - in.seg[j]) + kB - 1) / kB;
+  Carve cs;
+  const size_t s_cnt = cs.take<uint32_t>(P_all + 1);
+  const size_t s_start = cs.take<uint32_t>(P_all + 1);
+  const size_t s_cursor = cs.take<uint32_t>(P_all + 1);
+  const size_t s_lb = cs.take<uint64_t>(P_all + 1);
+  const size_t s_ticket = cs.take<uint32_t>(4);
+  const size_t s_ovl = cs.take<uint32_t>(P_all + 1);
+  const size_t s_ove = cs.take<uint64_t>(P_all + 1);
+  const size_t s_skey = cs.take<uint64_t>(total);
+  const size_t s_spay = cs.take<uint64_t>(total * PW);
+  const size_t s_maps = cs.take<MapDev>(m);
+  const size_t s_pseg = cs.take<uint64_t>(m + 1);
+  const size_t s_qseg = cs.take<uint32_t>(m + 1);
+  const size_t s_stat = cs.take<MapStatus>(m);
+  const size_t s_fps = cs.take<uint64_t>(str ? total + 1 : 0);
+  uint8_t* scr = static_cast<uint8_t*>(A.get(cs.off, st));
+  if (!scr) {
+    A.put(block, cm.off, st);
+    return fail(FKS_ERR_OUT_OF_MEMORY, "allocation of build scratch failed");
+  }
+  uint64_t* ovf_key = nullptr;
+  size_t ovf_bytes = 0;
+
+  PassDev p{};
+  p.part_cnt = reinterpret_cast<uint32_t*>(scr + s_cnt);
+  p.part_start = reinterpret_cast<uint32_t*>(scr + s_start);
+  p.part_cursor = reinterpret_cast<uint32_t*>(scr + s_cursor);
+  p.lookback = reinterpret_cast<uint64_t*>(scr + s_lb);
+  p.ticket = reinterpret_cast<uint32_t*>(scr + s_ticket);
+  p.ovf_count = p.ticket + 1;
+  p.ovf_list = reinterpret_cast<uint32_t*>(scr + s_ovl);
+  p.ovf_excl = reinterpret_cast<uint64_t*>(scr + s_ove);
+  p.stage_key = reinterpret_cast<uint64_t*>(scr + s_skey);
+  p.stage_pay = reinterpret_cast<uint64_t*>(scr + s_spay);
+  MapDev* d_maps = reinterpret_cast<MapDev*>(scr + s_maps);
+  uint64_t* d_pseg = reinterpret_cast<uint64_t*>(scr + s_pseg);
+  uint32_t* d_qseg = reinterpret_cast<uint32_t*>(scr + s_qseg);
+  MapStatus* d_stat = reinterpret_cast<MapStatus*>(scr + s_stat);
+  uint64_t* fps = str ? reinterpret_cast<uint64_t*>(scr + s_fps) : nullptr;
+  p.maps = d_maps;
+  p.status = d_stat;
+  p.pass_seg = d_pseg;
+  p.part_seg = d_qseg;
+  p.hkeys = str ? fps : in.keys;
+  p.vals = in.vals;
+  p.vals_i64 = in.vt == FKS_VAL_I64;
+  p.offs = in.offs;
+  p.ctx = mem->ctx;
+  p.desc = mem->desc;
+  p.slots = mem->slots;
+  p.cfg.attempt_cap = o.attempt_cap;
+  p.cfg.reject = o.reject;
+  p.cfg.spin_limit = o.spin;
+  p.cfg.hold_first = uint32_t(g_hold_first_partition);
+
+  std::vector<uint32_t> round(m, 0);
+  std::vector<uint32_t> active(m);
+  for (uint32_t j = 0; j < m; ++j) active[j] = j;
+  per_map->assign(m, FKS_OK);
+  maps_out->assign(m, fks_map());
+  std::vector<uint32_t> exhausted;  // maps whose rounds all failed
+  fks_status hard = FKS_OK;         // a failure of the whole call
+  std::string hard_msg;
+  const int sms = sm_count();
+  ProfileEvents prof;
+  fks_build_profile profile{};
+
+  auto cleanup = [&]() {
+    if (ovf_key) A.put(ovf_key, ovf_bytes, st);
+    A.put(scr, cs.off, st);
+  };
+
+  while (!active.empty() && hard == FKS_OK) {
+    const uint32_t ma = uint32_t(active.size());
+    // ---- pass tables
+    const size_t up_bytes = sizeof(MapDev) * ma + sizeof(uint64_t) * (ma + 1) + sizeof(uint32_t) * (ma + 1);
+    uint8_t* up = static_cast<uint8_t*>(g_pin_up.get(up_bytes));
+    if (!up) { hard = FKS_ERR_CUDA; hard_msg = "pinned staging"; break; }
+    MapDev* h_maps = reinterpret_cast<MapDev*>(up);
+    uint64_t* h_pseg = reinterpret_cast<uint64_t*>(up + sizeof(MapDev) * ma);
+    uint32_t* h_qseg = reinterpret_cast<uint32_t*>(up + sizeof(MapDev) * ma + sizeof(uint64_t) * (ma + 1));
+    uint64_t pe = 0;
+    uint32_t pp = 0;
+    for (uint32_t a = 0; a < ma; ++a) {
+      const uint32_t j = active[a];
+      const uint64_t n = uint64_t(in.seg[j + 1] - in.seg[j]);
+      MapDev& M = h_maps[a];
+      M.key_begin = uint64_t(in.seg[j]);
+      M.pass_begin = pe;
+      M.desc_base = uint64_t(in.seg[j]);
+      M.slot_base = slot_base[j];
+      M.seed = in.seeds[j];
+      M.round = round[j];
+      M.c1 = derive(M.seed, M.round, kTagLevel1, 0);
+      M.fpb = fp_base(M.seed, M.round);
+      M.n = uint32_t(n);
+      M.slot_cap = uint32_t(uint64_t(o.bound) * n);
+      M.part_begin = pp;
+      h_pseg[a] = pe;
+      h_qseg[a] = pp;
+      pe += n;
+      pp += uint32_t((n + kB - 1) / kB);
+    }
+    h_pseg[ma] = pe;
+    h_qseg[ma] = pp;
+    p.m = ma;
+    p.P = pp;
+    p.total = pe;
+    cudaError_t e;
+#define FKS_PASS(call)                                  \
+  if ((e = (call)) != cudaSuccess) {                    \
+    hard = FKS_ERR_CUDA;                                \
+    hard_msg = std::string(#call ": ") + cudaGetErrorString(e); \
+    break;                                              \
+  }
+    FKS_PASS(cudaMemcpyAsync(d_maps, h_maps, sizeof(MapDev) * ma, cudaMemcpyHostToDevice, st));
+    FKS_PASS(cudaMemcpyAsync(d_pseg, h_pseg, sizeof(uint64_t) * (ma + 1), cudaMemcpyHostToDevice, st));
+    FKS_PASS(cudaMemcpyAsync(d_qseg, h_qseg, sizeof(uint32_t) * (ma + 1), cudaMemcpyHostToDevice, st));
+    FKS_PASS(cudaMemsetAsync(d_stat, 0, sizeof(MapStatus) * ma, st));
+    if (prof.ok && str) cudaEventRecord(prof.fp0, st);
+    if (str) FKS_PASS(launch_fingerprints(in.ctx, in.offs, total, d_maps, d_pseg, ma, pe, fps, d_stat, st));
+    if (prof.ok && str) cudaEventRecord(prof.fp1, st);
+    FKS_PASS(launch_pass(p, str, sms, st, prof.ok ? &prof.pe : nullptr));
+    // ---- status
+    const size_t down_bytes = sizeof(MapStatus) * ma + 16;
+    uint8_t* down = static_cast<uint8_t*>(g_pin_down.get(down_bytes));
+    if (!down) { hard = FKS_ERR_CUDA; hard_msg = "pinned staging"; break; }
+    MapStatus* h_stat = reinterpret_cast<MapStatus*>(down);
+    uint32_t* h_ovf = reinterpret_cast<uint32_t*>(down + sizeof(MapStatus) * ma);
+    FKS_PASS(cudaMemcpyAsync(h_stat, d_stat, sizeof(MapStatus) * ma, cudaMemcpyDeviceToHost, st));
+    FKS_PASS(cudaMemcpyAsync(h_ovf, p.ovf_count, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    FKS_PASS(cudaStreamSynchronize(st));
+    prof.accumulate(&profile, str);
+    if (*h_ovf) {
+      if (!ovf_key) {
+        ovf_bytes = sizeof(uint64_t) * (total * (1 + PW) + 2);
+        ovf_key = static_cast<uint64_t*>(A.get(ovf_bytes, st));
+        if (!ovf_key) { hard = FKS_ERR_OUT_OF_MEMORY; hard_msg = "overflow buffer"; break; }
+      }
+      p.ovf_key = ovf_key;
+      p.ovf_pay = ovf_key + total;
+      FKS_PASS(launch_overflow(p, str, *h_ovf, st));
+      FKS_PASS(cudaMemcpyAsync(h_stat, d_stat, sizeof(MapStatus) * ma, cudaMemcpyDeviceToHost, st));
+      FKS_PASS(cudaStreamSynchronize(st));
+    }
+#undef FKS_PASS
+    // ---- decide per map
+    std::vector<uint32_t> next;
+    for (uint32_t a = 0; a < ma; ++a) {
+      const uint32_t j = active[a];
+      const MapStatus& S = h_stat[a];
+      if (S.invalid) {
+        (*per_map)[j] = FKS_ERR_INVALID_ARG;
+        continue;
+      }
+      if (S.timeout) {
+        (*per_map)[j] = FKS_ERR_TIMEOUT;
+        continue;
+      }
+      bool redo = false;
+      if (S.reseed) redo = true;
+      else if (S.dup) {
+        (*per_map)[j] = FKS_ERR_DUPLICATE_KEY;
+        continue;
+      } else if (S.next_round) redo = true;
+      if (redo) {
+        if (round[j] + 1 >= o.round_cap) exhausted.push_back(j);
+        else {
+          round[j] += 1;
+          next.push_back(j);
+        }
+        continue;
+      }
+      fks_map& M = (*maps_out)[j];
+      M.kind = in.kind;
+      M.vt = in.vt;
+      M.n = uint64_t(in.seg[j + 1] - in.seg[j]);
+      M.seed = in.seeds[j];
+      M.round = round[j];
+      M.c1 = h_maps[a].c1;
+      M.fpb = h_maps[a].fpb;
+      M.S = S.S;
+      M.slot_cap = uint64_t(o.bound) * M.n;
+      M.att_sum = S.att_sum;
+      M.max_s = S.max_s;
+      M.max_att = S.max_att;
+      M.overflow = S.overflow;
+      M.nonempty = S.nonempty;
+      M.desc = mem->desc + in.seg[j];
+      M.slots = mem->slots + slot_base[j] * W;
+      M.ctx = mem->ctx;
+      M.ctx_bytes = ctx_bytes;
+      M.bytes = sizeof(uint64_t) * (M.n + W * M.slot_cap);
+    }
+    active.swap(next);
+  }
+  // ---- maps whose every round failed: exact duplicate test
+  for (uint32_t j : exhausted) {
+    if (hard != FKS_OK) break;
+    const uint64_t n = uint64_t(in.seg[j + 1] - in.seg[j]);
+    uint64_t size = 1;
+    while (size < 2 * n) size <<= 1;
+    const size_t tb = sizeof(uint64_t) * size + (str ? sizeof(uint32_t) * size : 0) + 64;
+    uint8_t* tbl = static_cast<uint8_t*>(A.get(tb, st));
+    if (!tbl) { hard = FKS_ERR_OUT_OF_MEMORY; hard_msg = "duplicate test table"; break; }
+    uint64_t* table = reinterpret_cast<uint64_t*>(tbl);
+    uint32_t* tidx = str ? reinterpret_cast<uint32_t*>(tbl + sizeof(uint64_t) * size) : nullptr;
+    uint32_t* flags = reinterpret_cast<uint32_t*>(tbl + tb - 64);
+    const uint64_t* hk = str ? fps + in.seg[j] : in.keys + in.seg[j];
+    cudaError_t e = launch_dupcheck(hk, str ? in.offs + in.seg[j] : nullptr, in.ctx, n, table, tidx,
+                                    size, flags, o.spin, st);
+    uint32_t hf[4] = {0, 0, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    A.put(tbl, tb, st);
+    if (e != cudaSuccess) {
+      hard = FKS_ERR_CUDA;
+      hard_msg = std::string("duplicate test: ") + cudaGetErrorString(e);
+      break;
+    }
+    (*per_map)[j] = hf[2] ? FKS_ERR_TIMEOUT : (hf[0] ? FKS_ERR_DUPLICATE_KEY : FKS_ERR_BUILD_FAILED);
+  }
+  cleanup();
+  if (prof.ok) g_last_profile = profile;
+  if (hard != FKS_OK) {
+    A.put(block, cm.off, st);
+    return fail(hard, hard_msg);
+  }
+  *out_block = block;
+  *out_block_bytes = cm.off;
+  return FKS_OK;
+}
+
+static const char* status_name(fks_status s) {
+  switch (s) {
+    case FKS_OK: return "ok";
+    case FKS_ERR_INVALID_ARG: return "invalid argument";
+    case FKS_ERR_DUPLICATE_KEY: return "duplicate key";
+    case FKS_ERR_OUT_OF_MEMORY: return "out of memory";
+    case FKS_ERR_BUILD_FAILED: return "build failed";
+    case FKS_ERR_TIMEOUT: return "device wait timed out";
+    case FKS_ERR_CUDA: return "CUDA error";
+    case FKS_ERR_EVICTED: return "map evicted";
+  }
+  return "unknown status";
+}
+
+static fks_status build_single(const BuildIn& in, const fks_build_opts* opts,
+                               const fks_allocator* alloc, cudaStream_t st, fks_map_t* out) {
+  Opts o;
+  if (!read_opts(opts, &o)) return fail(FKS_ERR_INVALID_ARG, "bad build options");
+  Alloc A(alloc);
+  void* block = nullptr;
+  size_t bb = 0;
+  SetMem mem;
+  std::vector<fks_map> maps;
+  std::vector<fks_status> per;
+  sm_count();
+  fks_status s = build_impl(in, o, A, st, &block, &bb, &mem, &maps, &per);
+  if (s != FKS_OK) return s;
+  if (per[0] != FKS_OK) {
+    A.put(block, bb, st);
+    return fail(per[0], std::string("build: ") + status_name(per[0]));
+  }
+  fks_map* m = new fks_map(maps[0]);
+  m->block = block;
+  m->block_bytes = bb;
+  m->alloc = A;
+  m->bytes = bb;
+  *out = m;
+  return FKS_OK;
+}
+
+// ================================================================ C ABI
+extern "C" {
+
+fks_status fks_build_u64(const uint64_t* keys, const void* vals, fks_val_type val_type, uint64_t n,
+                         uint64_t seed, const fks_build_opts* opts, const fks_allocator* alloc,
+                         fks_stream_t stream, fks_map_t* out) {
+  if (!out) return fail(FKS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!keys || !vals || n == 0 || n >= (1ull << 30) ||
+      (val_type != FKS_VAL_I32 && val_type != FKS_VAL_I64))
+    return fail(FKS_ERR_INVALID_ARG, "fks_build_u64: bad keys, vals, n or val_type");
+  const int64_t seg[2] = {0, int64_t(n)};
+  BuildIn in{FKS_KEY_U64, keys, nullptr, nullptr, vals, val_type, 1, seg, &seed};
+  return build_single(in, opts, alloc, reinterpret_cast<cudaStream_t>(stream), out);
+}
+
+fks_status fks_build_bytes(const uint8_t* ctx, const int64_t* offs, const void* vals,
+                           fks_val_type val_type, uint64_t n, uint64_t seed,
+                           const fks_build_opts* opts, const fks_allocator* alloc,
+                           fks_stream_t stream, fks_map_t* out) {
+  if (!out) return fail(FKS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!ctx || !offs || !vals || n == 0 || n >= (1ull << 30) ||
+      (val_type != FKS_VAL_I32 && val_type != FKS_VAL_I64))
+    return fail(FKS_ERR_INVALID_ARG, "fks_build_bytes: bad ctx, offs, vals, n or val_type");
+  const int64_t seg[2] = {0, int64_t(n)};
+  BuildIn in{FKS_KEY_BYTES, nullptr, ctx, offs, vals, val_type, 1, seg, &seed};
+  return build_single(in, opts, alloc, reinterpret_cast<cudaStream_t>(stream), out);
+}
+
+static bool absent_fits(const fks_map* m, int64_t absent) {
+  return m->vt == FKS_VAL_I64 || (absent >= INT32_MIN && absent <= INT32_MAX);
+}
+
+fks_status fks_lookup_u64(fks_map_t map, const uint64_t* q, uint64_t nq, void* out_vals,
+                          uint8_t* out_found, int64_t absent, fks_stream_t stream) {
+  if (!map || map->kind != FKS_KEY_U64) return fail(FKS_ERR_INVALID_ARG, "fks_lookup_u64: not a u64 map");
+  if (nq == 0) return FKS_OK;
+  if (!q || !absent_fits(map, absent)) return fail(FKS_ERR_INVALID_ARG, "fks_lookup_u64: bad arguments");
+  FKS_CUDA(launch_lookup_u64(lookup_view(*map), q, nq, out_vals, map->vt == FKS_VAL_I64, out_found,
+                             absent, sm_count(), reinterpret_cast<cudaStream_t>(stream)));
+  return FKS_OK;
+}
+
+fks_status fks_lookup_bytes(fks_map_t map, const uint8_t* qctx, const int64_t* qoffs, uint64_t nq,
+                            void* out_vals, uint8_t* out_found, int64_t absent,
+                            fks_stream_t stream) {
+  if (!map || map->kind != FKS_KEY_BYTES) return fail(FKS_ERR_INVALID_ARG, "fks_lookup_bytes: not a string map");
+  if (nq == 0) return FKS_OK;
+  if (!qctx || !qoffs || !absent_fits(map, absent))
+    return fail(FKS_ERR_INVALID_ARG, "fks_lookup_bytes: bad arguments");
+  FKS_CUDA(launch_lookup_bytes(lookup_view(*map), qctx, qoffs, nq, out_vals, map->vt == FKS_VAL_I64,
+                               out_found, absent, sm_count(), reinterpret_cast<cudaStream_t>(stream)));
+  return FKS_OK;
+}
+
+fks_status fks_build_batched(fks_key_kind kind, const uint64_t* keys, const uint8_t* ctx,
+                             const int64_t* offs, const int64_t* h_seg, const uint64_t* h_seeds,
+                             uint32_t m, const void* vals, fks_val_type val_type,
+                             const fks_build_opts* opts, const fks_allocator* alloc,
+                             fks_stream_t stream, fks_mapset_t* out, fks_status* h_status) {
+  if (!out) return fail(FKS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (m == 0 || !h_seg || !h_seeds || !vals || (val_type != FKS_VAL_I32 && val_type != FKS_VAL_I64))
+    return fail(FKS_ERR_INVALID_ARG, "fks_build_batched: bad arguments");
+  if (kind == FKS_KEY_U64 ? !keys : (kind == FKS_KEY_BYTES ? (!ctx || !offs) : true))
+    return fail(FKS_ERR_INVALID_ARG, "fks_build_batched: bad key arguments");
+  if (h_seg[0] != 0) return fail(FKS_ERR_INVALID_ARG, "fks_build_batched: h_seg[0] != 0");
+  for (uint32_t j = 0; j < m; ++j) {
+    const int64_t n = h_seg[j + 1] - h_seg[j];
+    if (n <= 0 || n >= (int64_t(1) << 30))
+      return fail(FKS_ERR_INVALID_ARG, "fks_build_batched: empty or oversized segment");
+  }
+  if (uint64_t(h_seg[m]) >= (1ull << 32))
+    return fail(FKS_ERR_INVALID_ARG, "fks_build_batched: 2^32 keys or more");
+  Opts o;
+  if (!read_opts(opts, &o)) return fail(FKS_ERR_INVALID_ARG, "bad build options");
+  Alloc A(alloc);
+  const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  BuildIn in{kind, keys, ctx, offs, vals, val_type, m, h_seg, h_seeds};
+  void* block = nullptr;
+  size_t bb = 0;
+  SetMem mem;
+  std::vector<fks_map> maps;
+  std::vector<fks_status> per;
+  sm_count();
+  fks_status s = build_impl(in, o, A, st, &block, &bb, &mem, &maps, &per);
+  if (s != FKS_OK) return s;
+  fks_status worst = FKS_OK;
+  for (uint32_t j = 0; j < m; ++j) {
+    if (h_status) h_status[j] = per[j];
+    if (per[j] != FKS_OK && worst == FKS_OK) worst = per[j];
+  }
+  fks_mapset* set = new fks_mapset();
+  set->kind = kind;
+  set->vt = val_type;
+  set->maps = std::move(maps);
+  set->block = block;
+  set->block_bytes = bb;
+  set->alloc = A;
+  // device table for batched lookups (maps that failed keep n = 0: always absent)
+  std::vector<LookupMap> tab(m);
+  for (uint32_t j = 0; j < m; ++j) {
+    if (per[j] == FKS_OK) tab[j] = lookup_view(set->maps[j]);
+    else {
+      memset(&tab[j], 0, sizeof(LookupMap));
+      tab[j].desc = mem.desc + h_seg[j];
+      tab[j].n = 1;  // a single empty bucket
+    }
+  }
+  // failed maps: make their first descriptor an empty bucket
+  for (uint32_t j = 0; j < m; ++j)
+    if (per[j] != FKS_OK) cudaMemsetAsync(mem.desc + h_seg[j], 0, sizeof(uint64_t), st);
+  set->d_table = static_cast<LookupMap*>(A.get(sizeof(LookupMap) * m, st));
+  if (!set->d_table) {
+    fks_mapset_destroy(set);
+    return fail(FKS_ERR_OUT_OF_MEMORY, "lookup table");
+  }
+  cudaError_t e = cudaMemcpyAsync(set->d_table, tab.data(), sizeof(LookupMap) * m,
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    fks_mapset_destroy(set);
+    return cuda_fail(e, "lookup table upload");
+  }
+  *out = set;
+  if (worst != FKS_OK) g_last_error = std::string("fks_build_batched: ") + status_name(worst);
+  return worst;
+}
+
+fks_status fks_lookup_batched(fks_mapset_t set, const uint32_t* map_ids, const uint64_t* q,
+                              const uint8_t* qctx, const int64_t* qoffs, uint64_t nq,
+                              void* out_vals, uint8_t* out_found, int64_t absent,
+                              fks_stream_t stream) {
+  if (!set) return fail(FKS_ERR_INVALID_ARG, "fks_lookup_batched: set is NULL");
+  if (nq == 0) return FKS_OK;
+  const bool str = set->kind == FKS_KEY_BYTES;
+  if (!map_ids || (str ? (!qctx || !qoffs) : !q))
+    return fail(FKS_ERR_INVALID_ARG, "fks_lookup_batched: bad arguments");
+  if (set->vt == FKS_VAL_I32 && (absent < INT32_MIN || absent > INT32_MAX))
+    return fail(FKS_ERR_INVALID_ARG, "fks_lookup_batched: absent does not fit int32");
+  FKS_CUDA(launch_lookup_batched(set->d_table, uint32_t(set->maps.size()), str, map_ids, q, qctx,
+                                 qoffs, nq, out_vals, set->vt == FKS_VAL_I64, out_found, absent,
+                                 sm_count(), reinterpret_cast<cudaStream_t>(stream)));
+  return FKS_OK;
+}
+
+uint32_t fks_mapset_size(fks_mapset_t set) { return set ? uint32_t(set->maps.size()) : 0u; }
+
+fks_map_t fks_mapset_get(fks_mapset_t set, uint32_t j) {
+  if (!set || j >= set->maps.size() || set->maps[j].n == 0) return nullptr;
+  return &set->maps[j];
+}
+
+fks_status fks_map_info(fks_map_t map, fks_map_info_t* h_out) {
+  if (!map || !h_out) return fail(FKS_ERR_INVALID_ARG, "fks_map_info: NULL argument");
+  memset(h_out, 0, sizeof(*h_out));
+  h_out->n = map->n;
+  h_out->seed = map->seed;
+  h_out->slots = map->S;
+  h_out->slot_capacity = map->slot_cap;
+  h_out->bytes = map->bytes;
+  h_out->attempts_sum = map->att_sum;
+  h_out->context_bytes = map->ctx_bytes;
+  h_out->round = map->round;
+  h_out->max_bucket = map->max_s;
+  h_out->max_attempt = map->max_att;
+  h_out->key_kind = map->kind;
+  h_out->val_type = map->vt;
+  h_out->overflow_partitions = map->overflow;
+  h_out->nonempty_buckets = map->nonempty;
+  return FKS_OK;
+}
+
+fks_status fks_map_export(fks_map_t map, uint64_t* h_desc, void* h_slots, uint8_t* h_ctx,
+                          fks_stream_t stream) {
+  if (!map) return fail(FKS_ERR_INVALID_ARG, "fks_map_export: NULL map");
+  const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int W = map->kind == FKS_KEY_BYTES ? 4 : 2;
+  if (h_desc) FKS_CUDA(cudaMemcpyAsync(h_desc, map->desc, sizeof(uint64_t) * map->n, cudaMemcpyDeviceToHost, st));
+  if (h_slots && map->S)
+    FKS_CUDA(cudaMemcpyAsync(h_slots, map->slots, sizeof(uint64_t) * W * map->S, cudaMemcpyDeviceToHost, st));
+  if (h_ctx && map->kind == FKS_KEY_BYTES && map->ctx_bytes)
+    FKS_CUDA(cudaMemcpyAsync(h_ctx, map->ctx, map->ctx_bytes, cudaMemcpyDeviceToHost, st));
+  FKS_CUDA(cudaStreamSynchronize(st));
+  return FKS_OK;
+}
+
+void fks_map_destroy(fks_map_t map) {
+  if (!map || !map->block) return;  // borrowed maps are freed with their set
+  map->alloc.put(map->block, map->block_bytes, nullptr);
+  delete map;
+}
+
+void fks_mapset_destroy(fks_mapset_t set) {
+  if (!set) return;
+  if (set->d_table) set->alloc.put(set->d_table, sizeof(LookupMap) * set->maps.size(), nullptr);
+  if (set->block) set->alloc.put(set->block, set->block_bytes, nullptr);
+  delete set;
+}
+
+const char* fks_status_str(fks_status status) { return status_name(status); }
+
+const char* fks_last_error(void) { return g_last_error.c_str(); }
+
+void fks_profile_enable(int on) {
+  g_profile = on;
+  if (on) g_last_profile = fks_build_profile{};
+}
+
+fks_status fks_last_build_profile(fks_build_profile* h_out) {
+  if (!h_out) return fail(FKS_ERR_INVALID_ARG, "fks_last_build_profile: NULL");
+  *h_out = g_last_profile;
+  return FKS_OK;
+}
+
+uint64_t fks_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

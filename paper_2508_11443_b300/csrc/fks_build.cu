@@ -1,0 +1,890 @@
+// fks_build.cu -- device construction of FKS two-level hash maps.
+//
+// The paper's data-parallel construction (Sec. 2.3-2.5) groups keys by their
+// level-one hash with Hist + Groupby (the sortless form tags every key with
+// its bucket and re-runs only the buckets that collided).  On sm_103a the
+// same steps are arranged around the memory hierarchy:
+//
+//   pass 1  k_partition<count>   g k for every key; keys per partition of
+//                                kB = 1024 consecutive buckets (L2 atomics on
+//                                a small counter array, warp-aggregated)
+//   pass 2  k_scan_parts         exclusive scan of the partition counts
+//   pass 3  k_partition<scatter> keys (+ payload) scattered into contiguous
+//                                partition ranges
+//   pass 4  k_part_build         one CTA per partition, a persistent work
+//                                queue: Hist of the partition's buckets in
+//                                shared memory, exclusive Presum of s and s^2,
+//                                a decoupled look-back across partitions for
+//                                the map-level slot offsets (Presum shape),
+//                                Groupby into shared memory, level-two search
+//                                per bucket (make_2: the first attempt with no
+//                                collision inside s^2 slots), descriptors and
+//                                slot image written out coalesced.
+//
+// The level-one space bound (sum s^2 <= bound * n) is checked on the running
+// slot prefix; a map that exceeds it is redrawn by the host (next round).
+// Partitions with more keys than shared memory holds are deferred to
+// k_part_overflow, which runs the same steps on global memory.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fks_internal.cuh"
+
+namespace fks {
+namespace {
+
+constexpr int kUnroll = 4;
+constexpr uint64_t kLbFlagA = 1ull << 62;
+constexpr uint64_t kLbFlagP = 2ull << 62;
+constexpr uint64_t kLbVal = (1ull << 62) - 1;
+constexpr uint64_t kSat = 1ull << 61;
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+__device__ __forceinline__ uint64_t ld_relaxed(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(uint64_t* p, uint64_t v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t sat(uint64_t x) { return x < kSat ? x : kSat; }
+
+template <class T>
+__device__ __forceinline__ uint32_t upper_seg(const T* seg, uint32_t m, uint64_t e) {
+  // largest j in [0, m) with seg[j] <= e  (seg[0] = 0 <= e < seg[m])
+  uint32_t lo = 0, hi = m;
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (uint64_t(seg[mid]) <= e) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int64_t load_val(const void* vals, int i64, uint64_t i) {
+  return i64 ? __ldg(static_cast<const long long*>(vals) + i)
+             : int64_t(__ldg(static_cast<const int*>(vals) + i));
+}
+
+// t-th little-endian 32-bit word of the byte string s[0 .. len), zero padded.
+// Reads only aligned words that hold at least one byte of the string.
+__device__ __forceinline__ uint32_t str_word(const uint8_t* s, uint32_t len, uint32_t t) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(s) + 4u * t;
+  const uint32_t r = len - 4u * t;  // bytes left, >= 1
+  const uint32_t take = r < 4u ? r : 4u;
+  const uint32_t sh = uint32_t(a & 3u);
+  const uint32_t* A = reinterpret_cast<const uint32_t*>(a & ~uintptr_t(3));
+  const uint32_t lo = __ldg(A);
+  const uint32_t hi = (sh + take > 4u) ? __ldg(A + 1) : 0u;
+  uint32_t w = __funnelshift_r(lo, hi, sh * 8u);
+  if (take < 4u) w &= (1u << (8u * take)) - 1u;
+  return w;
+}
+
+__device__ __forceinline__ uint64_t fingerprint(const uint8_t* s, uint32_t len, uint64_t base) {
+  uint64_t h = len;
+  const uint32_t words = (len + 3u) >> 2;
+  for (uint32_t t = 0; t < words; ++t) h = addmod61(mulmod61(h, base), str_word(s, len, t));
+  return h;
+}
+
+__device__ __forceinline__ bool bytes_equal(const uint8_t* a, const uint8_t* b, uint32_t len) {
+  const uint32_t words = (len + 3u) >> 2;
+  for (uint32_t t = 0; t < words; ++t)
+    if (str_word(a, len, t) != str_word(b, len, t)) return false;
+  return true;
+}
+
+// -------------------------------------------------------------- fingerprints
+__global__ void __launch_bounds__(256) k_fingerprints(const uint8_t* __restrict__ ctx,
+                                                      const int64_t* __restrict__ offs,
+                                                      const MapDev* __restrict__ maps,
+                                                      const uint64_t* __restrict__ pass_seg,
+                                                      uint32_t m, uint64_t total,
+                                                      uint64_t* __restrict__ fps,
+                                                      MapStatus* status) {
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t e = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += stride) {
+    const uint32_t j = m == 1 ? 0u : upper_seg(pass_seg, m, e);
+    const MapDev& M = maps[j];
+    const uint64_t in = M.key_begin + (e - M.pass_begin);
+    const int64_t o0 = __ldg(reinterpret_cast<const long long*>(offs) + in);
+    const int64_t o1 = __ldg(reinterpret_cast<const long long*>(offs) + in + 1);
+    const int64_t len = o1 - o0;
+    if (o0 < 0 || len < 0 || len >= (int64_t(1) << 24) || o1 >= (int64_t(1) << 40)) {
+      atomicExch(&status[j].invalid, 1u);
+      fps[in] = 0;
+      continue;
+    }
+    fps[in] = fingerprint(ctx + o0, uint32_t(len), M.fpb);
+  }
+}
+
+// -------------------------------------------------------------- partitioning
+// Warp-aggregated claim of `count` consecutive cells of ctr[idx]: lanes with
+// the same idx share one atomic (the paper's Hist, Sec. 2.1, with atomics).
+template <bool kNeedPos>
+__device__ __forceinline__ uint32_t claim(uint32_t* ctr, uint32_t idx, bool valid, bool agg) {
+  if (!agg) {
+    if (!valid) return 0;
+    if (kNeedPos) return atomicAdd(ctr + idx, 1u);
+    atomicAdd(ctr + idx, 1u);
+    return 0;
+  }
+  const uint32_t key = valid ? idx : 0xFFFFFFFFu;
+  const uint32_t peers = __match_any_sync(0xFFFFFFFFu, key);
+  const uint32_t leader = __ffs(peers) - 1;
+  uint32_t base = 0;
+  if (valid && lane_id() == leader) {
+    if (kNeedPos) base = atomicAdd(ctr + idx, uint32_t(__popc(peers)));
+    else atomicAdd(ctr + idx, uint32_t(__popc(peers)));
+  }
+  if (!kNeedPos) return 0;
+  base = __shfl_sync(peers, base, leader);
+  return base + __popc(peers & lanemask_lt());
+}
+
+template <bool kScatter, bool kStr>
+__global__ void __launch_bounds__(256) k_partition(PassDev p, int agg) {
+  extern __shared__ uint64_t sh_seg[];
+  const uint64_t* seg = p.pass_seg;
+  if (p.m > 1 && p.m <= 2048) {
+    for (uint32_t i = threadIdx.x; i <= p.m; i += blockDim.x) sh_seg[i] = p.pass_seg[i];
+    __syncthreads();
+    seg = sh_seg;
+  }
+  const uint32_t lane = lane_id();
+  const uint64_t warp0 = (uint64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31u)) * kUnroll;
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x * kUnroll;
+  const MapDev* maps = p.maps;
+  for (uint64_t base = warp0; base < p.total; base += stride) {
+    uint64_t k[kUnroll], in[kUnroll];
+    uint32_t gp[kUnroll];
+    bool ok[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const uint64_t e = base + uint64_t(u) * 32 + lane;
+      ok[u] = e < p.total;
+      uint32_t j = 0;
+      if (ok[u] && p.m > 1) j = upper_seg(seg, p.m, e);
+      const uint64_t kb = maps[j].key_begin, pb = maps[j].pass_begin;
+      in[u] = kb + (e - pb);
+      k[u] = ok[u] ? __ldg(reinterpret_cast<const unsigned long long*>(p.hkeys) + in[u]) : 0;
+      const HashConsts c1 = maps[j].c1;
+      const uint32_t b = reduce32(hash32(c1, k[u]), maps[j].n);
+      gp[u] = maps[j].part_begin + (b >> kLogB);
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      if (!kScatter) {
+        claim<false>(p.part_cnt, gp[u], ok[u], agg);
+      } else {
+        const uint32_t pos = claim<true>(p.part_cursor, gp[u], ok[u], agg);
+        if (ok[u]) {
+          p.stage_key[pos] = k[u];
+          const int64_t v = load_val(p.vals, p.vals_i64, in[u]);
+          if (!kStr) {
+            p.stage_pay[pos] = uint64_t(v);
+          } else {
+            const int64_t o0 = __ldg(reinterpret_cast<const long long*>(p.offs) + in[u]);
+            const int64_t o1 = __ldg(reinterpret_cast<const long long*>(p.offs) + in[u] + 1);
+            reinterpret_cast<ulonglong2*>(p.stage_pay)[pos] =
+                make_ulonglong2(offlen_pack(uint64_t(o0), uint64_t(o1 - o0)), uint64_t(v));
+          }
+        }
+      }
+    }
+  }
+}
+
+// One CTA: exclusive scan of the partition counts; clears the look-back words,
+// the work-queue head and the overflow counter for the build kernel.
+__global__ void __launch_bounds__(1024) k_scan_parts(PassDev p) {
+  __shared__ uint32_t wsum[32];
+  const uint32_t T = blockDim.x, t = threadIdx.x;
+  const uint32_t per = (p.P + T - 1) / T;
+  const uint32_t lo = min(p.P, t * per), hi = min(p.P, lo + per);
+  uint32_t sum = 0;
+  for (uint32_t i = lo; i < hi; ++i) {
+    sum += p.part_cnt[i];
+    p.lookback[i] = 0;
+  }
+  uint32_t incl = sum;
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t x = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+    if (lane_id() >= uint32_t(d)) incl += x;
+  }
+  if (lane_id() == 31) wsum[t >> 5] = incl;
+  __syncthreads();
+  if (t < 32) {
+    uint32_t w = t < (T >> 5) ? wsum[t] : 0u, wi = w;
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t x = __shfl_up_sync(0xFFFFFFFFu, wi, d);
+      if (t >= uint32_t(d)) wi += x;
+    }
+    wsum[t] = wi - w;
+  }
+  __syncthreads();
+  uint32_t run = wsum[t >> 5] + incl - sum;
+  for (uint32_t i = lo; i < hi; ++i) {
+    p.part_start[i] = run;
+    p.part_cursor[i] = run;
+    run += p.part_cnt[i];
+  }
+  if (t == T - 1) p.part_start[p.P] = run;
+  if (t == 0) {
+    *p.ticket = 0;
+    *p.ovf_count = 0;
+  }
+}
+
+// -------------------------------------------------------------- partition CTA
+template <int PW>
+struct Smem {
+  static constexpr uint32_t kGkey = 0;
+  static constexpr uint32_t kGpay = kGkey + kCap * 8;
+  static constexpr uint32_t kOwner = kGpay + kCap * 8 * PW;
+  static constexpr uint32_t kCnt = kOwner + kOwnerCap * 2;
+  static constexpr uint32_t kGst = kCnt + kB * 4;
+  static constexpr uint32_t kSoff = kGst + (kB + 4) * 4;
+  static constexpr uint32_t kAtt = kSoff + kB * 4;
+  static constexpr uint32_t kBytes = kAtt + kB * 2;
+};
+
+struct PartCtl {
+  uint32_t gp, j, skip, nbig, maxs, maxatt, flag_a, flag_b, nonempty;
+  uint64_t excl, Spart, attsum;
+  unsigned long long fillmin;  // (slot << 32) | member of a CTA-searched bucket
+  uint32_t wsum[kPartThreads / 32];
+  uint64_t wsum2[kPartThreads / 32];
+};
+
+struct MapRegs {
+  HashConsts c1;
+  uint64_t seed, desc_base, slot_base;
+  uint32_t n, round, slot_cap, part_begin, part_end;
+};
+
+__device__ __forceinline__ MapRegs load_map(const PassDev& p, uint32_t j) {
+  const MapDev& M = p.maps[j];
+  MapRegs r;
+  r.c1 = M.c1;
+  r.seed = M.seed;
+  r.desc_base = M.desc_base;
+  r.slot_base = M.slot_base;
+  r.n = M.n;
+  r.round = M.round;
+  r.slot_cap = M.slot_cap;
+  r.part_begin = M.part_begin;
+  r.part_end = p.part_seg[j + 1];
+  return r;
+}
+
+// Hist of the partition's buckets + exclusive Presum of s and s^2.
+// Leaves cnt[] holding s, gst[] the group starts (gst[kB] = keys), soff[] the
+// partition-local slot offsets, and ctl.Spart = sum s^2.
+template <int PW>
+__device__ void count_and_scan(const PassDev& p, const MapRegs& M, uint32_t b0, uint64_t e0,
+                               uint64_t e1, uint32_t* cnt, uint32_t* gst, uint32_t* soff,
+                               PartCtl& ctl) {
+  const uint32_t t = threadIdx.x;
+  for (uint32_t i = t; i < kB; i += kPartThreads) cnt[i] = 0;
+  __syncthreads();
+  for (uint64_t e = e0 + t; e < e1; e += kPartThreads) {
+    const uint64_t k = p.stage_key[e];
+    const uint32_t lb = reduce32(hash32(M.c1, k), M.n) - b0;
+    atomicAdd(cnt + lb, 1u);
+  }
+  __syncthreads();
+  constexpr uint32_t kPer = kB / kPartThreads;
+  uint32_t c[kPer], ls = 0, mx = 0, ne = 0;
+  uint64_t ls2 = 0;
+#pragma unroll
+  for (uint32_t i = 0; i < kPer; ++i) {
+    c[i] = cnt[t * kPer + i];
+    ls += c[i];
+    ls2 += uint64_t(c[i]) * c[i];
+    mx = max(mx, c[i]);
+    ne += c[i] != 0;
+  }
+  ne = __reduce_add_sync(0xFFFFFFFFu, ne);
+  if (lane_id() == 0) atomicAdd(&ctl.nonempty, ne);
+  uint32_t inc = ls;
+  uint64_t inc2 = ls2;
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t x = __shfl_up_sync(0xFFFFFFFFu, inc, d);
+    const uint64_t x2 = __shfl_up_sync(0xFFFFFFFFu, inc2, d);
+    if (lane_id() >= uint32_t(d)) {
+      inc += x;
+      inc2 += x2;
+    }
+  }
+  for (int d = 16; d > 0; d >>= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, d));
+  if (lane_id() == 31) {
+    ctl.wsum[t >> 5] = inc;
+    ctl.wsum2[t >> 5] = inc2;
+  }
+  if (lane_id() == 0) atomicMax(&ctl.maxs, mx);
+  __syncthreads();
+  uint32_t we = 0;
+  uint64_t we2 = 0;
+  for (uint32_t w = 0; w < (t >> 5); ++w) {
+    we += ctl.wsum[w];
+    we2 += ctl.wsum2[w];
+  }
+  uint32_t run = we + inc - ls;
+  uint64_t run2 = we2 + inc2 - ls2;
+#pragma unroll
+  for (uint32_t i = 0; i < kPer; ++i) {
+    gst[t * kPer + i] = run;
+    soff[t * kPer + i] = uint32_t(run2 < 0xFFFFFFFFull ? run2 : 0xFFFFFFFFull);
+    run += c[i];
+    run2 += uint64_t(c[i]) * c[i];
+  }
+  if (t == kPartThreads - 1) {
+    gst[kB] = run;
+    ctl.Spart = run2;
+  }
+  __syncthreads();
+}
+
+// Decoupled look-back (thread 0): exclusive slot prefix of partition gp within
+// its map.  Every wait is bounded by cfg.spin_limit polls.
+__device__ uint64_t look_back(const PassDev& p, uint32_t gp, uint32_t first, uint64_t agg,
+                              bool* timed_out) {
+  const bool hold = p.cfg.hold_first && gp == 0;
+  if (gp == first) {
+    if (!hold) st_relaxed(p.lookback + gp, kLbFlagP | sat(agg));
+    return 0;
+  }
+  if (!hold) st_relaxed(p.lookback + gp, kLbFlagA | sat(agg));
+  uint64_t excl = 0;
+  uint32_t q = gp - 1, polls = 0, ns = 32;
+  for (;;) {
+    const uint64_t w = ld_relaxed(p.lookback + q);
+    if (w == 0) {
+      if (++polls > p.cfg.spin_limit) {
+        *timed_out = true;
+        excl = kSat;
+        break;
+      }
+      __nanosleep(ns);
+      if (ns < 1024) ns <<= 1;
+      continue;
+    }
+    excl = sat(excl + (w & kLbVal));
+    if ((w >> 62) == 2 || q == first) break;
+    --q;
+  }
+  if (!hold) st_relaxed(p.lookback + gp, kLbFlagP | sat(excl + agg));
+  return excl;
+}
+
+// Equal keys of two members: u64 maps compare keys; string maps compare bytes.
+template <int PW>
+__device__ __forceinline__ bool same_member(const PassDev& p, const uint64_t* gpay, uint32_t x,
+                                            uint32_t y) {
+  if (PW == 1) return true;  // called only for equal keys
+  const uint64_t ox = gpay[2 * x], oy = gpay[2 * y];
+  const uint32_t lx = offlen_len(ox), ly = offlen_len(oy);
+  if (lx != ly) return false;
+  return bytes_equal(p.ctx + offlen_off(ox), p.ctx + offlen_off(oy), lx);
+}
+
+enum { kSearchDup = -1, kSearchNext = -2 };
+
+// make_2 for one bucket by one thread: the first attempt whose s hashes
+// into s^2 slots are pairwise distinct.
+template <int PW>
+__device__ int search_thread(const PassDev& p, const uint64_t* k, const uint64_t* gpay,
+                             uint32_t g0, uint32_t s, uint64_t seed, uint32_t round, uint32_t b) {
+  const uint32_t m = s * s;
+  for (uint32_t a = 0; a < p.cfg.attempt_cap; ++a) {
+    if (a == kDupCheckAttempt) {
+      bool eq = false, dup = false;
+      for (uint32_t x = 0; x < s; ++x)
+        for (uint32_t y = x + 1; y < s; ++y)
+          if (k[x] == k[y]) {
+            eq = true;
+            dup |= same_member<PW>(p, gpay, g0 + x, g0 + y);
+          }
+      if (dup) return kSearchDup;
+      if (eq) return kSearchNext;
+    }
+    const HashConsts c = derive(seed, round, b, a);
+    bool col = false;
+    if (s <= 8) {
+      uint64_t bits = 0;
+      for (uint32_t x = 0; x < s; ++x) {
+        const uint64_t bit = 1ull << reduce32(hash32(c, k[x]), m);
+        col |= (bits & bit) != 0;
+        bits |= bit;
+      }
+    } else {
+      uint16_t js[kThreadSearchMax];
+      for (uint32_t x = 0; x < s; ++x) {
+        js[x] = uint16_t(reduce32(hash32(c, k[x]), m));
+        for (uint32_t y = 0; y < x; ++y) col |= js[y] == js[x];
+      }
+    }
+    if (a < p.cfg.reject) continue;
+    if (!col) return int(a);
+  }
+  return kSearchNext;
+}
+
+template <int PW>
+__device__ __forceinline__ void write_slot(const PassDev& p, uint64_t idx, uint64_t key,
+                                           const uint64_t* pay, bool fill) {
+  if (PW == 1) {
+    reinterpret_cast<ulonglong2*>(p.slots)[idx] = make_ulonglong2(key, fill ? ~0ull : pay[0]);
+  } else {
+    ulonglong2* d = reinterpret_cast<ulonglong2*>(p.slots) + 2 * idx;
+    d[0] = make_ulonglong2(key, pay[0]);
+    d[1] = make_ulonglong2(fill ? ~0ull : pay[1], 0ull);
+  }
+}
+
+// Place one searched bucket (thread level).  owner mode: record member /
+// filler indices in the shared slot image; else write the slots directly.
+template <int PW>
+__device__ void place_thread(const PassDev& p, const uint64_t* k, const uint64_t* gpay,
+                             uint32_t g0, uint32_t s, const HashConsts& c, uint16_t* owner,
+                             uint32_t so, uint64_t slot0, bool owner_mode) {
+  const uint32_t m = s * s;
+  uint32_t jmin = 0xFFFFFFFFu, xmin = 0;
+  for (uint32_t x = 0; x < s; ++x) {
+    const uint32_t jj = reduce32(hash32(c, k[x]), m);
+    if (jj < jmin) {
+      jmin = jj;
+      xmin = x;
+    }
+    if (owner_mode) owner[so + jj] = uint16_t(g0 + x);
+  }
+  if (owner_mode) {
+    for (uint32_t t = 0; t < m; ++t)
+      if (owner[so + t] == kOwnerEmpty) owner[so + t] = uint16_t(kOwnerFill | (g0 + xmin));
+  } else {
+    if (s > 1)
+      for (uint32_t t = 0; t < m; ++t) write_slot<PW>(p, slot0 + t, k[xmin], gpay + PW * (g0 + xmin), true);
+    for (uint32_t x = 0; x < s; ++x)
+      write_slot<PW>(p, slot0 + reduce32(hash32(c, k[x]), m), k[x], gpay + PW * (g0 + x), false);
+  }
+}
+
+// make_2 + placement for a bucket larger than kThreadSearchMax, by the CTA.
+template <int PW>
+__device__ void search_place_cta(const PassDev& p, const uint64_t* k, const uint64_t* gpay,
+                                 uint32_t g0, uint32_t s, uint64_t seed, uint32_t round,
+                                 uint32_t b, uint16_t* owner, uint32_t so, uint64_t slot0,
+                                 bool owner_mode, uint32_t j, PartCtl& ctl, uint16_t* att_out) {
+  const uint32_t t = threadIdx.x, m = s * s;
+  int found = kSearchNext;
+  for (uint32_t a = 0; a < p.cfg.attempt_cap; ++a) {
+    if (a == kDupCheckAttempt) {
+      if (t == 0) ctl.flag_a = ctl.flag_b = 0;
+      __syncthreads();
+      for (uint32_t x = t; x < s; x += kPartThreads)
+        for (uint32_t y = x + 1; y < s; ++y)
+          if (k[x] == k[y]) {
+            ctl.flag_a = 1;
+            if (same_member<PW>(p, gpay, g0 + x, g0 + y)) ctl.flag_b = 1;
+          }
+      __syncthreads();
+      const uint32_t eq = ctl.flag_a, dup = ctl.flag_b;
+      __syncthreads();
+      if (dup) { found = kSearchDup; break; }
+      if (eq) { found = kSearchNext; break; }
+    }
+    const HashConsts c = derive(seed, round, b, a);
+    if (t == 0) ctl.flag_a = 0;
+    __syncthreads();
+    for (uint32_t x = t; x < s && !ctl.flag_a; x += kPartThreads) {
+      const uint32_t jx = reduce32(hash32(c, k[x]), m);
+      for (uint32_t y = 0; y < s; ++y)
+        if (y != x && reduce32(hash32(c, k[y]), m) == jx) {
+          ctl.flag_a = 1;
+          break;
+        }
+    }
+    __syncthreads();
+    const uint32_t col = ctl.flag_a;
+    __syncthreads();
+    if (a >= p.cfg.reject && !col) { found = int(a); break; }
+  }
+  if (found < 0) {
+    if (t == 0) {
+      if (found == kSearchDup) atomicExch(&p.status[j].dup, 1u);
+      else atomicExch(&p.status[j].next_round, 1u);
+      *att_out = 0;
+    }
+    __syncthreads();
+    return;
+  }
+  const HashConsts c = derive(seed, round, b, uint32_t(found));
+  if (t == 0) {
+    *att_out = uint16_t(found);
+    ctl.fillmin = ~0ull;
+    atomicMax(&ctl.maxatt, uint32_t(found));
+    ctl.attsum += uint64_t(found);
+  }
+  __syncthreads();
+  // filler = member with the lowest slot
+  for (uint32_t x = t; x < s; x += kPartThreads) {
+    const uint32_t jx = reduce32(hash32(c, k[x]), m);
+    atomicMin(&ctl.fillmin, (static_cast<unsigned long long>(jx) << 32) | x);
+  }
+  __syncthreads();
+  const uint32_t xmin = uint32_t(ctl.fillmin & 0xFFFFFFFFull);
+  if (owner_mode) {
+    for (uint32_t x = t; x < s; x += kPartThreads) owner[so + reduce32(hash32(c, k[x]), m)] = uint16_t(g0 + x);
+    __syncthreads();
+    for (uint32_t q = t; q < m; q += kPartThreads)
+      if (owner[so + q] == kOwnerEmpty) owner[so + q] = uint16_t(kOwnerFill | (g0 + xmin));
+  } else {
+    for (uint32_t q = t; q < m; q += kPartThreads)
+      write_slot<PW>(p, slot0 + q, k[xmin], gpay + PW * (g0 + xmin), true);
+    __syncthreads();
+    for (uint32_t x = t; x < s; x += kPartThreads)
+      write_slot<PW>(p, slot0 + reduce32(hash32(c, k[x]), m), k[x], gpay + PW * (g0 + x), false);
+  }
+  __syncthreads();
+}
+
+// Groupby, level-two search, descriptors and slots of one partition whose
+// counts/scan are already in shared memory.  gkey/gpay point at the grouped
+// buffer (shared memory, or global memory for an overflow partition).
+template <int PW>
+__device__ void group_search_write(const PassDev& p, const MapRegs& M, uint32_t j, uint32_t b0,
+                                   uint32_t nb, uint64_t e0, uint64_t e1, uint64_t excl,
+                                   uint64_t* gkey, uint64_t* gpay, uint16_t* owner, uint32_t* cnt,
+                                   const uint32_t* gst, const uint32_t* soff, uint16_t* att,
+                                   PartCtl& ctl) {
+  const uint32_t t = threadIdx.x;
+  const uint64_t Sp = ctl.Spart;
+  const bool owner_mode = Sp <= kOwnerCap;
+  for (uint32_t i = t; i < kB; i += kPartThreads) cnt[i] = gst[i];
+  if (owner_mode)
+    for (uint32_t q = t; q < uint32_t(Sp); q += kPartThreads) owner[q] = kOwnerEmpty;
+  if (t == 0) ctl.nbig = 0;
+  __syncthreads();
+  // Groupby: scatter the partition's keys to their bucket's group.
+  for (uint64_t e = e0 + t; e < e1; e += kPartThreads) {
+    const uint64_t k = p.stage_key[e];
+    const uint32_t lb = reduce32(hash32(M.c1, k), M.n) - b0;
+    const uint32_t pos = atomicAdd(cnt + lb, 1u);
+    gkey[pos] = k;
+#pragma unroll
+    for (int w = 0; w < PW; ++w) gpay[PW * pos + w] = p.stage_pay[PW * e + w];
+  }
+  __syncthreads();
+  const uint64_t slot_part = M.slot_base + excl;  // slot index of partition-local slot 0
+  uint32_t my_max = 0;
+  uint64_t my_sum = 0;
+  for (uint32_t lb = t; lb < nb; lb += kPartThreads) {
+    const uint32_t g0 = gst[lb], s = gst[lb + 1] - g0;
+    uint16_t a_out = 0;
+    if (s == 1) {
+      if (owner_mode) owner[soff[lb]] = uint16_t(g0);
+      else write_slot<PW>(p, slot_part + soff[lb], gkey[g0], gpay + PW * g0, false);
+    } else if (s > 1 && s <= kThreadSearchMax) {
+      const int a = search_thread<PW>(p, gkey + g0, gpay, g0, s, M.seed, M.round, b0 + lb);
+      if (a >= 0) {
+        a_out = uint16_t(a);
+        my_max = max(my_max, uint32_t(a));
+        my_sum += uint64_t(a);
+        const HashConsts c = derive(M.seed, M.round, b0 + lb, uint32_t(a));
+        place_thread<PW>(p, gkey + g0, gpay, g0, s, c, owner, soff[lb], slot_part + soff[lb],
+                         owner_mode);
+      } else if (a == kSearchDup) {
+        atomicExch(&p.status[j].dup, 1u);
+      } else {
+        atomicExch(&p.status[j].next_round, 1u);
+      }
+    } else if (s > kThreadSearchMax) {
+      atomicAdd(&ctl.nbig, 1u);  // searched below by the whole CTA
+    }
+    att[lb] = a_out;
+  }
+  if (my_max) atomicMax(&ctl.maxatt, my_max);
+  if (my_sum) atomicAdd(reinterpret_cast<unsigned long long*>(&ctl.attsum), my_sum);
+  __syncthreads();
+  if (ctl.nbig) {
+    for (uint32_t lb = 0; lb < nb; ++lb) {  // uniform over the CTA
+      const uint32_t g0 = gst[lb], s = gst[lb + 1] - g0;
+      if (s <= kThreadSearchMax) continue;
+      search_place_cta<PW>(p, gkey + g0, gpay, g0, s, M.seed, M.round, b0 + lb, owner, soff[lb],
+                           slot_part + soff[lb], owner_mode, j, ctl, att + lb);
+    }
+  }
+  __syncthreads();
+  // descriptors of the partition's buckets (coalesced)
+  for (uint32_t lb = t; lb < nb; lb += kPartThreads) {
+    const uint32_t s = gst[lb + 1] - gst[lb];
+    p.desc[M.desc_base + b0 + lb] = desc_pack(uint32_t(excl + soff[lb]), s, att[lb]);
+  }
+  // slot image (coalesced)
+  if (owner_mode) {
+    for (uint32_t q = t; q < uint32_t(Sp); q += kPartThreads) {
+      const uint16_t o = owner[q];
+      const uint32_t idx = o & 0x7FFFu;
+      write_slot<PW>(p, slot_part + q, gkey[idx], gpay + PW * idx, (o & kOwnerFill) != 0);
+    }
+  }
+}
+
+template <int PW>
+__global__ void __launch_bounds__(kPartThreads) k_part_build(PassDev p) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  using L = Smem<PW>;
+  uint64_t* gkey = reinterpret_cast<uint64_t*>(smem + L::kGkey);
+  uint64_t* gpay = reinterpret_cast<uint64_t*>(smem + L::kGpay);
+  uint16_t* owner = reinterpret_cast<uint16_t*>(smem + L::kOwner);
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(smem + L::kCnt);
+  uint32_t* gst = reinterpret_cast<uint32_t*>(smem + L::kGst);
+  uint32_t* soff = reinterpret_cast<uint32_t*>(smem + L::kSoff);
+  uint16_t* att = reinterpret_cast<uint16_t*>(smem + L::kAtt);
+  __shared__ PartCtl ctl;
+  const uint32_t t = threadIdx.x;
+  for (;;) {
+    __syncthreads();
+    if (t == 0) {
+      ctl.gp = atomicAdd(p.ticket, 1u);
+      ctl.nonempty = 0;
+      ctl.maxs = 0;
+      ctl.maxatt = 0;
+      ctl.attsum = 0;
+    }
+    __syncthreads();
+    const uint32_t gp = ctl.gp;
+    if (gp >= p.P) return;
+    const uint32_t j = p.m == 1 ? 0u : upper_seg(p.part_seg, p.m, gp);
+    const MapRegs M = load_map(p, j);
+    const uint32_t b0 = (gp - M.part_begin) << kLogB;
+    const uint32_t nb = min(kB, M.n - b0);
+    const uint64_t e0 = p.part_start[gp], e1 = p.part_start[gp + 1];
+    count_and_scan<PW>(p, M, b0, e0, e1, cnt, gst, soff, ctl);
+    if (t == 0) {
+      bool to = false;
+      const uint64_t excl = look_back(p, gp, M.part_begin, ctl.Spart, &to);
+      ctl.excl = excl;
+      const uint64_t incl = excl + ctl.Spart;
+      ctl.skip = (to || incl > M.slot_cap) ? 1u : 0u;
+      if (to) atomicExch(&p.status[j].timeout, 1u);
+      if (incl > M.slot_cap) atomicExch(&p.status[j].reseed, 1u);
+      if (gp + 1 == M.part_end) p.status[j].S = incl;
+      atomicMax(&p.status[j].max_s, ctl.maxs);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&p.status[j].nonempty),
+                (unsigned long long)ctl.nonempty);
+    }
+    __syncthreads();
+    if (ctl.skip) continue;
+    if (e1 - e0 > kCap) {
+      if (t == 0) {
+        const uint32_t slot = atomicAdd(p.ovf_count, 1u);
+        p.ovf_list[slot] = gp;
+        p.ovf_excl[slot] = ctl.excl;
+        atomicAdd(&p.status[j].overflow, 1u);
+      }
+      continue;
+    }
+    group_search_write<PW>(p, M, j, b0, nb, e0, e1, ctl.excl, gkey, gpay, owner, cnt, gst, soff,
+                           att, ctl);
+    __syncthreads();
+    if (t == 0) {
+      if (ctl.maxatt) atomicMax(&p.status[j].max_att, ctl.maxatt);
+      if (ctl.attsum) atomicAdd(reinterpret_cast<unsigned long long*>(&p.status[j].att_sum),
+                                (unsigned long long)ctl.attsum);
+    }
+  }
+}
+
+// Partitions deferred because they hold more than kCap keys: grouped through
+// global memory (the rare, adversarial case).
+template <int PW>
+__global__ void __launch_bounds__(kPartThreads) k_part_overflow(PassDev p) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  using L = Smem<PW>;
+  uint16_t* owner = reinterpret_cast<uint16_t*>(smem + L::kOwner);
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(smem + L::kCnt);
+  uint32_t* gst = reinterpret_cast<uint32_t*>(smem + L::kGst);
+  uint32_t* soff = reinterpret_cast<uint32_t*>(smem + L::kSoff);
+  uint16_t* att = reinterpret_cast<uint16_t*>(smem + L::kAtt);
+  __shared__ PartCtl ctl;
+  const uint32_t t = threadIdx.x;
+  const uint32_t gp = p.ovf_list[blockIdx.x];
+  if (t == 0) {
+    ctl.maxs = 0;
+    ctl.maxatt = 0;
+    ctl.attsum = 0;
+    ctl.nonempty = 0;
+  }
+  __syncthreads();
+  const uint32_t j = p.m == 1 ? 0u : upper_seg(p.part_seg, p.m, gp);
+  const MapRegs M = load_map(p, j);
+  const uint32_t b0 = (gp - M.part_begin) << kLogB;
+  const uint32_t nb = min(kB, M.n - b0);
+  const uint64_t e0 = p.part_start[gp], e1 = p.part_start[gp + 1];
+  count_and_scan<PW>(p, M, b0, e0, e1, cnt, gst, soff, ctl);
+  const uint64_t excl = p.ovf_excl[blockIdx.x];
+  // group indices are partition-local; the grouped buffer starts at e0
+  group_search_write<PW>(p, M, j, b0, nb, e0, e1, excl, p.ovf_key + e0, p.ovf_pay + PW * e0,
+                         owner, cnt, gst, soff, att, ctl);
+  __syncthreads();
+  if (t == 0) {
+    if (ctl.maxatt) atomicMax(&p.status[j].max_att, ctl.maxatt);
+    if (ctl.attsum) atomicAdd(reinterpret_cast<unsigned long long*>(&p.status[j].att_sum),
+                              (unsigned long long)ctl.attsum);
+  }
+}
+
+// -------------------------------------------------------------- duplicate test
+// Exact global duplicate test after every level-one round failed: insertion
+// into an open-addressing set; flags[0] = duplicate found, flags[1] = keys
+// equal to the empty marker (u64 maps), flags[2] = a wait ran out.
+__global__ void __launch_bounds__(256) k_dupcheck(const uint64_t* __restrict__ hkeys,
+                                                  const int64_t* __restrict__ offs,
+                                                  const uint8_t* __restrict__ ctx, uint64_t n,
+                                                  uint64_t* table, uint32_t* tidx,
+                                                  uint64_t size, uint32_t* flags,
+                                                  uint32_t spin_limit) {
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  const uint64_t mask = size - 1;
+  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint64_t k = hkeys[i];
+    if (!offs && k == ~0ull) {
+      if (atomicAdd(flags + 1, 1u) >= 1u) atomicExch(flags, 1u);
+      continue;
+    }
+    uint64_t h = mix13(k) & mask;
+    for (uint64_t probe = 0; probe < size; ++probe, h = (h + 1) & mask) {
+      const uint64_t old = atomicCAS(reinterpret_cast<unsigned long long*>(table + h), ~0ull, k);
+      if (old == ~0ull) {
+        if (offs) atomicExch(tidx + h, uint32_t(i + 1));
+        break;
+      }
+      if (old != k) continue;
+      if (!offs) {
+        atomicExch(flags, 1u);
+        break;
+      }
+      uint32_t other = 0, polls = 0;
+      while ((other = atomicAdd(tidx + h, 0u)) == 0u) {
+        if (++polls > spin_limit) break;
+        __nanosleep(64);
+      }
+      if (other == 0u) {
+        atomicExch(flags + 2, 1u);
+        break;
+      }
+      const uint64_t oi = other - 1;
+      const int64_t li = offs[i + 1] - offs[i], lo = offs[oi + 1] - offs[oi];
+      if (li == lo && bytes_equal(ctx + offs[i], ctx + offs[oi], uint32_t(li))) {
+        atomicExch(flags, 1u);
+        break;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+// ================================================================ launchers
+cudaError_t launch_fingerprints(const uint8_t* ctx, const int64_t* offs, uint64_t n,
+                                const MapDev* maps, const uint64_t* pass_seg, uint32_t m,
+                                uint64_t total, uint64_t* fps, MapStatus* status,
+                                cudaStream_t stream) {
+  (void)n;
+  if (total == 0) return cudaSuccess;
+  const uint64_t blocks = (total + 255) / 256;
+  k_fingerprints<<<unsigned(blocks < 65535ull * 16 ? blocks : 65535ull * 16), 256, 0, stream>>>(
+      ctx, offs, maps, pass_seg, m, total, fps, status);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+template <int PW>
+static cudaError_t launch_build_kernel(const PassDev& p, int sms, cudaStream_t stream) {
+  static int occ = -1;
+  const int smem = int(Smem<PW>::kBytes);
+  if (occ < 0) {
+    cudaError_t e = cudaFuncSetAttribute(k_part_build<PW>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_part_overflow<PW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem);
+    if (e != cudaSuccess) return e;
+    int o = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_part_build<PW>, kPartThreads, smem);
+    if (e != cudaSuccess) return e;
+    occ = o > 0 ? o : 1;
+  }
+  const uint64_t want = uint64_t(sms) * occ;
+  const unsigned grid = unsigned(p.P < want ? p.P : want);
+  k_part_build<PW><<<grid, kPartThreads, smem, stream>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pass(const PassDev& p, bool strings, int sms, cudaStream_t stream,
+                        const PassEvents* ev) {
+  if (p.total == 0 || p.P == 0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(p.part_cnt, 0, sizeof(uint32_t) * p.P, stream);
+  if (e != cudaSuccess) return e;
+  if (ev) cudaEventRecord(ev->ev[0], stream);
+  // Warp aggregation pays off when a warp's keys share partitions (small maps).
+  const int agg = (p.total / p.P) < 64 || p.P < 64 ? 1 : 0;
+  const size_t seg_smem = (p.m > 1 && p.m <= 2048) ? sizeof(uint64_t) * (p.m + 1) : 0;
+  uint64_t blocks = (p.total + 256 * kUnroll - 1) / (256 * kUnroll);
+  const uint64_t maxb = uint64_t(sms) * 8;
+  if (blocks > maxb) blocks = maxb;
+  if (strings) k_partition<false, true><<<unsigned(blocks), 256, seg_smem, stream>>>(p, agg);
+  else k_partition<false, false><<<unsigned(blocks), 256, seg_smem, stream>>>(p, agg);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (ev) cudaEventRecord(ev->ev[1], stream);
+  k_scan_parts<<<1, 1024, 0, stream>>>(p);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (ev) cudaEventRecord(ev->ev[2], stream);
+  if (strings) k_partition<true, true><<<unsigned(blocks), 256, seg_smem, stream>>>(p, agg);
+  else k_partition<true, false><<<unsigned(blocks), 256, seg_smem, stream>>>(p, agg);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (ev) cudaEventRecord(ev->ev[3], stream);
+  e = strings ? launch_build_kernel<2>(p, sms, stream) : launch_build_kernel<1>(p, sms, stream);
+  if (e != cudaSuccess) return e;
+  if (ev) cudaEventRecord(ev->ev[4], stream);
+  note_launches(4);
+  return cudaSuccess;
+}
+
+cudaError_t launch_overflow(const PassDev& p, bool strings, uint32_t count, cudaStream_t stream) {
+  if (count == 0) return cudaSuccess;
+  if (strings) {
+    k_part_overflow<2><<<count, kPartThreads, Smem<2>::kBytes, stream>>>(p);
+  } else {
+    k_part_overflow<1><<<count, kPartThreads, Smem<1>::kBytes, stream>>>(p);
+  }
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dupcheck(const uint64_t* hkeys, const int64_t* offs, const uint8_t* ctx,
+                            uint64_t n, uint64_t* table, uint32_t* table_idx, uint64_t table_size,
+                            uint32_t* flags, uint32_t spin_limit, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(table, 0xFF, sizeof(uint64_t) * table_size, stream);
+  if (e != cudaSuccess) return e;
+  if (table_idx && (e = cudaMemsetAsync(table_idx, 0, sizeof(uint32_t) * table_size, stream)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemsetAsync(flags, 0, sizeof(uint32_t) * 4, stream)) != cudaSuccess) return e;
+  uint64_t blocks = (n + 255) / 256;
+  if (blocks > 148ull * 16) blocks = 148ull * 16;
+  k_dupcheck<<<unsigned(blocks), 256, 0, stream>>>(hkeys, offs, ctx, n, table, table_idx,
+                                                  table_size, flags, spin_limit);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace fks

@@ -1,0 +1,141 @@
+// fks_internal.cuh -- data structures shared by the kernels and the host side
+// of the library (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fks_device.cuh"
+
+namespace fks {
+
+// Level-one buckets are processed in partitions of kB consecutive buckets.
+// A partition's keys (about kB of them, since there are n buckets for n
+// keys) are grouped, searched and placed inside one CTA's shared memory.
+constexpr int kLogB = 10;
+constexpr uint32_t kB = 1u << kLogB;
+constexpr uint32_t kCap = 2048;        // keys of a partition held in shared memory
+constexpr uint32_t kOwnerCap = 4096;   // slots of a partition staged in shared memory
+constexpr int kPartThreads = 256;      // threads of a partition CTA
+constexpr uint32_t kThreadSearchMax = 64;  // larger buckets are searched by the whole CTA
+constexpr uint16_t kOwnerEmpty = 0xFFFF;
+constexpr uint16_t kOwnerFill = 0x8000;
+
+// One map of a build pass.  A pass builds a set of maps whose elements are
+// numbered 0 .. total-1 in pass order; map j owns pass elements
+// [pass_begin, pass_begin + n) which are input elements
+// [key_begin, key_begin + n).
+struct MapDev {
+  uint64_t key_begin;   // first input element (keys / fingerprints / values)
+  uint64_t pass_begin;  // first pass element
+  uint64_t desc_base;   // descriptor index of the map's bucket 0
+  uint64_t slot_base;   // slot index of the map's slot 0
+  uint64_t seed;
+  uint64_t fpb;         // fingerprint base of this round (string maps)
+  HashConsts c1;        // level-one constants of this round
+  uint32_t n;           // keys = level-one buckets
+  uint32_t round;
+  uint32_t slot_cap;    // bound_factor * n
+  uint32_t part_begin;  // first partition (pass numbering)
+};
+
+// Per-map outcome of a pass, written by the device.
+struct MapStatus {
+  uint32_t reseed;      // sum s^2 above the bound: next round
+  uint32_t dup;         // two equal keys in one bucket
+  uint32_t next_round;  // attempts exhausted / equal fingerprints of different strings
+  uint32_t timeout;     // a bounded wait ran out
+  uint32_t invalid;     // bad string offsets
+  uint32_t overflow;    // partitions deferred to the global-memory kernel
+  uint32_t max_s;
+  uint32_t max_att;
+  uint64_t S;           // sum s^2 (valid when reseed == 0)
+  uint64_t att_sum;
+  uint64_t nonempty;    // buckets with s > 0
+};
+
+struct BuildCfg {
+  uint32_t attempt_cap;
+  uint32_t reject;       // test hook: attempts below this count as failed
+  uint32_t spin_limit;   // polls of a look-back wait before giving up
+  uint32_t hold_first;   // test hook: partition 0 never publishes (forces a timeout)
+};
+
+// Everything a pass's kernels read; passed by value.
+struct PassDev {
+  const MapDev* maps;
+  MapStatus* status;
+  const uint64_t* pass_seg;   // [m+1] pass element offsets
+  const uint32_t* part_seg;   // [m+1] partition offsets
+  uint32_t m;
+  uint32_t P;                 // partitions
+  uint64_t total;             // pass elements
+  // inputs
+  const uint64_t* hkeys;      // u64 keys, or fingerprints of string keys (input numbering)
+  const void* vals;           // int32 / int64 values (input numbering)
+  const int64_t* offs;        // string maps: offsets (input numbering), else null
+  const uint8_t* ctx;         // string maps: the map set's own context copy
+  int vals_i64;
+  // scratch
+  uint32_t* part_cnt;         // [P]    keys per partition
+  uint32_t* part_start;       // [P+1]  exclusive scan of part_cnt
+  uint32_t* part_cursor;      // [P]    scatter cursors
+  uint64_t* lookback;         // [P]    decoupled look-back words
+  uint32_t* ticket;           // partition work queue head
+  uint64_t* stage_key;        // [total]
+  uint64_t* stage_pay;        // [total * PW]
+  uint32_t* ovf_list;         // [P] partitions deferred to the overflow kernel
+  uint64_t* ovf_excl;         // [P] their slot prefix
+  uint32_t* ovf_count;
+  uint64_t* ovf_key;          // [total]      (lazily allocated)
+  uint64_t* ovf_pay;          // [total * PW] (lazily allocated)
+  // outputs
+  uint64_t* desc;             // descriptor array of the set
+  uint64_t* slots;            // slot array of the set (2 or 4 words per slot)
+  BuildCfg cfg;
+};
+
+// Process-wide count of kernels launched by the library (fks_api.cu).
+void note_launches(uint32_t n);
+
+// Optional CUDA events recorded between the phases of a pass:
+// ev[0] before counting, ev[1] after counting, ev[2] after the scan,
+// ev[3] after the scatter, ev[4] after the partition build.
+struct PassEvents {
+  cudaEvent_t ev[5];
+};
+
+// Launchers (fks_build.cu).
+cudaError_t launch_fingerprints(const uint8_t* ctx, const int64_t* offs, uint64_t n,
+                                const MapDev* maps, const uint64_t* pass_seg, uint32_t m,
+                                uint64_t total, uint64_t* fps, MapStatus* status,
+                                cudaStream_t stream);
+cudaError_t launch_pass(const PassDev& p, bool strings, int sms, cudaStream_t stream,
+                        const PassEvents* events);
+cudaError_t launch_overflow(const PassDev& p, bool strings, uint32_t count, cudaStream_t stream);
+cudaError_t launch_dupcheck(const uint64_t* hkeys, const int64_t* offs, const uint8_t* ctx,
+                            uint64_t n, uint64_t* table, uint32_t* table_idx, uint64_t table_size,
+                            uint32_t* flags, uint32_t spin_limit, cudaStream_t stream);
+
+// Lookup side (fks_lookup.cu).
+struct LookupMap {
+  const uint64_t* desc;
+  const uint64_t* slots;   // 2 (u64) or 4 (bytes) words per slot
+  const uint8_t* ctx;      // string maps: the map's context
+  HashConsts c1;
+  uint64_t seed;
+  uint64_t fpb;
+  uint32_t n;
+  uint32_t round;
+};
+cudaError_t launch_lookup_u64(const LookupMap& M, const uint64_t* q, uint64_t nq, void* out,
+                              int out_i64, uint8_t* found, int64_t absent, int sms,
+                              cudaStream_t stream);
+cudaError_t launch_lookup_bytes(const LookupMap& M, const uint8_t* qctx, const int64_t* qoffs,
+                                uint64_t nq, void* out, int out_i64, uint8_t* found,
+                                int64_t absent, int sms, cudaStream_t stream);
+cudaError_t launch_lookup_batched(const LookupMap* maps, uint32_t m, int strings,
+                                  const uint32_t* ids, const uint64_t* q, const uint8_t* qctx,
+                                  const int64_t* qoffs, uint64_t nq, void* out, int out_i64,
+                                  uint8_t* found, int64_t absent, int sms, cudaStream_t stream);
+
+}  // namespace fks

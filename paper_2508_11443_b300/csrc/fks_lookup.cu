@@ -1,0 +1,302 @@
+// fks_lookup.cu -- lookups against FKS two-level hash maps.
+//
+// The membership test of Sec. 2.2 (arr[h a] = a) and lookup -> opt v of
+// Sec. 3.2: one dependent read of the bucket descriptor desc[g q], one
+// dependent read of the slot offsets[g q] + Hash consts[g q] q mod s^2, one
+// compare.  An empty bucket answers "absent" without the second read.
+//
+// The two reads are random 8 B / 16 B accesses into tables far larger than
+// L2, so the kernel is bound by DRAM sector throughput: each thread keeps
+// kQ queries in flight (all descriptor reads issued before any slot read),
+// queries are read and results written with vector accesses, and the random
+// reads bypass L1 allocation.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fks_internal.cuh"
+
+namespace fks {
+namespace {
+
+constexpr int kLookupThreads = 256;
+
+__device__ __forceinline__ uint64_t ld_na_u64(const uint64_t* p) {
+  uint64_t v;
+  asm volatile("ld.global.nc.L1::no_allocate.u64 %0, [%1];" : "=l"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ ulonglong2 ld_na_u128(const uint64_t* p) {
+  ulonglong2 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v2.u64 {%0, %1}, [%2];"
+               : "=l"(v.x), "=l"(v.y)
+               : "l"(p));
+  return v;
+}
+
+// t-th little-endian 32-bit word of s[0 .. len), zero padded; reads only
+// aligned words holding at least one byte of the string.
+__device__ __forceinline__ uint32_t str_word(const uint8_t* s, uint32_t len, uint32_t t) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(s) + 4u * t;
+  const uint32_t r = len - 4u * t;
+  const uint32_t take = r < 4u ? r : 4u;
+  const uint32_t sh = uint32_t(a & 3u);
+  const uint32_t* A = reinterpret_cast<const uint32_t*>(a & ~uintptr_t(3));
+  const uint32_t lo = __ldg(A);
+  const uint32_t hi = (sh + take > 4u) ? __ldg(A + 1) : 0u;
+  uint32_t w = __funnelshift_r(lo, hi, sh * 8u);
+  if (take < 4u) w &= (1u << (8u * take)) - 1u;
+  return w;
+}
+
+template <int kQ, bool kI64>
+__global__ void __launch_bounds__(kLookupThreads) k_lookup_u64(LookupMap M,
+                                                               const uint64_t* __restrict__ q,
+                                                               uint64_t nq, void* __restrict__ out,
+                                                               uint8_t* __restrict__ found,
+                                                               int64_t absent, int vec) {
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x * kQ;
+  for (uint64_t base = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) * kQ; base < nq;
+       base += stride) {
+    const bool full = vec && base + kQ <= nq;
+    uint64_t k[kQ];
+    if (full) {
+#pragma unroll
+      for (int i = 0; i < kQ; i += 2) {
+        const ulonglong2 v = __ldcs(reinterpret_cast<const ulonglong2*>(q + base + i));
+        k[i] = v.x;
+        k[i + 1] = v.y;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) k[i] = base + i < nq ? __ldcs(q + base + i) : 0;
+    }
+    uint32_t b[kQ];
+    uint64_t d[kQ];
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      b[i] = reduce32(hash32(M.c1, k[i]), M.n);
+      d[i] = ld_na_u64(M.desc + b[i]);
+    }
+    ulonglong2 sl[kQ];
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      const uint32_t s = desc_s(d[i]);
+      sl[i] = make_ulonglong2(~k[i], 0);
+      if (s) {
+        const HashConsts c = derive(M.seed, M.round, b[i], desc_attempt(d[i]));
+        const uint32_t jj = desc_off(d[i]) + reduce32(hash32(c, k[i]), s * s);
+        sl[i] = ld_na_u128(M.slots + 2ull * jj);
+      }
+    }
+    int64_t v[kQ];
+    uint32_t f = 0;
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      const bool hit = sl[i].x == k[i];
+      v[i] = hit ? int64_t(sl[i].y) : absent;
+      f |= uint32_t(hit) << (8 * i);
+    }
+    if (full) {
+      if (out) {
+        if (kI64) {
+#pragma unroll
+          for (int i = 0; i < kQ; i += 2)
+            __stcs(reinterpret_cast<longlong2*>(static_cast<int64_t*>(out) + base + i),
+                   make_longlong2(v[i], v[i + 1]));
+        } else {
+#pragma unroll
+          for (int i = 0; i < kQ; i += 4)
+            __stcs(reinterpret_cast<int4*>(static_cast<int32_t*>(out) + base + i),
+                   make_int4(int(v[i]), int(v[i + 1]), int(v[i + 2]), int(v[i + 3])));
+        }
+      }
+      if (found) {
+        if (kQ == 4) __stcs(reinterpret_cast<unsigned int*>(found + base), f);
+        else
+#pragma unroll
+          for (int i = 0; i < kQ; ++i) found[base + i] = uint8_t(f >> (8 * i));
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) {
+        if (base + i >= nq) break;
+        if (out) {
+          if (kI64) static_cast<int64_t*>(out)[base + i] = v[i];
+          else static_cast<int32_t*>(out)[base + i] = int32_t(v[i]);
+        }
+        if (found) found[base + i] = uint8_t(f >> (8 * i));
+      }
+    }
+  }
+}
+
+// One needle of a string map; returns whether it is present.
+__device__ __forceinline__ bool lookup_one_bytes(const LookupMap& M, const uint8_t* s,
+                                                 uint32_t len, int64_t* val) {
+  uint64_t h = len;
+  const uint32_t words = (len + 3u) >> 2;
+  for (uint32_t t = 0; t < words; ++t) h = addmod61(mulmod61(h, M.fpb), str_word(s, len, t));
+  const uint32_t b = reduce32(hash32(M.c1, h), M.n);
+  const uint64_t d = ld_na_u64(M.desc + b);
+  const uint32_t sz = desc_s(d);
+  if (!sz) return false;
+  const HashConsts c = derive(M.seed, M.round, b, desc_attempt(d));
+  const uint32_t jj = desc_off(d) + reduce32(hash32(c, h), sz * sz);
+  const ulonglong2 w0 = ld_na_u128(M.slots + 4ull * jj);
+  if (w0.x != h || offlen_len(w0.y) != len) return false;
+  const uint8_t* ms = M.ctx + offlen_off(w0.y);
+  for (uint32_t t = 0; t < words; ++t)
+    if (str_word(ms, len, t) != str_word(s, len, t)) return false;
+  *val = int64_t(ld_na_u64(M.slots + 4ull * jj + 2));
+  return true;
+}
+
+template <bool kI64>
+__global__ void __launch_bounds__(kLookupThreads) k_lookup_bytes(LookupMap M,
+                                                                 const uint8_t* __restrict__ qctx,
+                                                                 const int64_t* __restrict__ qoffs,
+                                                                 uint64_t nq, void* __restrict__ out,
+                                                                 uint8_t* __restrict__ found,
+                                                                 int64_t absent) {
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nq; i += stride) {
+    const int64_t o0 = __ldg(reinterpret_cast<const long long*>(qoffs) + i);
+    const int64_t o1 = __ldg(reinterpret_cast<const long long*>(qoffs) + i + 1);
+    int64_t v = absent;
+    bool hit = false;
+    if (o1 >= o0 && o1 - o0 < (int64_t(1) << 24)) hit = lookup_one_bytes(M, qctx + o0, uint32_t(o1 - o0), &v);
+    if (!hit) v = absent;
+    if (out) {
+      if (kI64) static_cast<int64_t*>(out)[i] = v;
+      else static_cast<int32_t*>(out)[i] = int32_t(v);
+    }
+    if (found) found[i] = uint8_t(hit);
+  }
+}
+
+// (map_id, needle) pairs against a set of maps; the small table of maps stays
+// in L1/L2.
+template <bool kI64, bool kStr>
+__global__ void __launch_bounds__(kLookupThreads) k_lookup_batched(
+    const LookupMap* __restrict__ maps, uint32_t m, const uint32_t* __restrict__ ids,
+    const uint64_t* __restrict__ q, const uint8_t* __restrict__ qctx,
+    const int64_t* __restrict__ qoffs, uint64_t nq, void* __restrict__ out,
+    uint8_t* __restrict__ found, int64_t absent) {
+  constexpr int kQ = 2;
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x * kQ;
+  for (uint64_t base = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) * kQ; base < nq;
+       base += stride) {
+    int64_t v[kQ];
+    bool hit[kQ];
+    if (!kStr) {
+      uint64_t k[kQ], d[kQ];
+      uint32_t b[kQ], id[kQ];
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) {
+        const bool ok = base + i < nq;
+        id[i] = ok ? __ldg(ids + base + i) : m;
+        k[i] = ok ? __ldcs(q + base + i) : 0;
+        d[i] = 0;
+        b[i] = 0;
+        if (id[i] < m) {
+          b[i] = reduce32(hash32(maps[id[i]].c1, k[i]), maps[id[i]].n);
+          d[i] = ld_na_u64(maps[id[i]].desc + b[i]);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) {
+        const uint32_t s = desc_s(d[i]);
+        hit[i] = false;
+        v[i] = absent;
+        if (s) {
+          const LookupMap& M = maps[id[i]];
+          const HashConsts c = derive(M.seed, M.round, b[i], desc_attempt(d[i]));
+          const uint32_t jj = desc_off(d[i]) + reduce32(hash32(c, k[i]), s * s);
+          const ulonglong2 sl = ld_na_u128(M.slots + 2ull * jj);
+          hit[i] = sl.x == k[i];
+          if (hit[i]) v[i] = int64_t(sl.y);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) {
+        hit[i] = false;
+        v[i] = absent;
+        if (base + i >= nq) continue;
+        const uint32_t id = __ldg(ids + base + i);
+        const int64_t o0 = __ldg(reinterpret_cast<const long long*>(qoffs) + base + i);
+        const int64_t o1 = __ldg(reinterpret_cast<const long long*>(qoffs) + base + i + 1);
+        if (id < m && o1 >= o0 && o1 - o0 < (int64_t(1) << 24))
+          hit[i] = lookup_one_bytes(maps[id], qctx + o0, uint32_t(o1 - o0), &v[i]);
+        if (!hit[i]) v[i] = absent;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      if (base + i >= nq) break;
+      if (out) {
+        if (kI64) static_cast<int64_t*>(out)[base + i] = v[i];
+        else static_cast<int32_t*>(out)[base + i] = int32_t(v[i]);
+      }
+      if (found) found[base + i] = uint8_t(hit[i]);
+    }
+  }
+}
+
+unsigned grid_for(uint64_t work, int sms, int per_sm) {
+  uint64_t blocks = (work + kLookupThreads - 1) / kLookupThreads;
+  const uint64_t cap = uint64_t(sms) * per_sm;
+  return unsigned(blocks < cap ? (blocks ? blocks : 1) : cap);
+}
+
+}  // namespace
+
+cudaError_t launch_lookup_u64(const LookupMap& M, const uint64_t* q, uint64_t nq, void* out,
+                              int out_i64, uint8_t* found, int64_t absent, int sms,
+                              cudaStream_t stream) {
+  if (nq == 0) return cudaSuccess;
+  constexpr int kQ = 4;
+  const int vec = ((reinterpret_cast<uintptr_t>(q) | reinterpret_cast<uintptr_t>(out) |
+                    reinterpret_cast<uintptr_t>(found)) & 15u) == 0;
+  const unsigned grid = grid_for((nq + kQ - 1) / kQ, sms, 8);
+  if (out_i64)
+    k_lookup_u64<kQ, true><<<grid, kLookupThreads, 0, stream>>>(M, q, nq, out, found, absent, vec);
+  else
+    k_lookup_u64<kQ, false><<<grid, kLookupThreads, 0, stream>>>(M, q, nq, out, found, absent, vec);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lookup_bytes(const LookupMap& M, const uint8_t* qctx, const int64_t* qoffs,
+                                uint64_t nq, void* out, int out_i64, uint8_t* found,
+                                int64_t absent, int sms, cudaStream_t stream) {
+  if (nq == 0) return cudaSuccess;
+  const unsigned grid = grid_for(nq, sms, 8);
+  if (out_i64)
+    k_lookup_bytes<true><<<grid, kLookupThreads, 0, stream>>>(M, qctx, qoffs, nq, out, found, absent);
+  else
+    k_lookup_bytes<false><<<grid, kLookupThreads, 0, stream>>>(M, qctx, qoffs, nq, out, found, absent);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lookup_batched(const LookupMap* maps, uint32_t m, int strings,
+                                  const uint32_t* ids, const uint64_t* q, const uint8_t* qctx,
+                                  const int64_t* qoffs, uint64_t nq, void* out, int out_i64,
+                                  uint8_t* found, int64_t absent, int sms, cudaStream_t stream) {
+  if (nq == 0) return cudaSuccess;
+  const unsigned grid = grid_for((nq + 1) / 2, sms, 8);
+#define FKS_LB(I64, STR)                                                                      \
+  k_lookup_batched<I64, STR><<<grid, kLookupThreads, 0, stream>>>(maps, m, ids, q, qctx, qoffs, \
+                                                                  nq, out, found, absent)
+  if (out_i64) {
+    if (strings) FKS_LB(true, true); else FKS_LB(true, false);
+  } else {
+    if (strings) FKS_LB(false, true); else FKS_LB(false, false);
+  }
+#undef FKS_LB
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace fks

@@ -1,0 +1,270 @@
+"""Thin Python binding of the C ABI in ``include/fks.h`` (argument marshalling only).
+
+Every function has the name of the C entry point it calls.  Device buffers
+are torch CUDA tensors (their ``data_ptr()`` is passed); the stream is the
+current torch stream unless one is given.  A non-OK status raises
+``FksError`` carrying the status and the library's message.  All work runs
+in the compiled library ``libfks.so``; there is no Python or CPU fallback, and
+importing this module without the compiled library fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libfks.so")
+
+FKS_OK = 0
+FKS_ERR_INVALID_ARG = 1
+FKS_ERR_DUPLICATE_KEY = 2
+FKS_ERR_OUT_OF_MEMORY = 3
+FKS_ERR_BUILD_FAILED = 4
+FKS_ERR_TIMEOUT = 5
+FKS_ERR_CUDA = 6
+FKS_ERR_EVICTED = 7
+FKS_VAL_I32, FKS_VAL_I64 = 0, 1
+FKS_KEY_U64, FKS_KEY_BYTES = 0, 1
+
+
+class FksError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"fks status {status}: {msg}")
+        self.status = status
+
+
+class fks_build_opts(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_size_t), ("bound_factor", ctypes.c_uint32),
+                ("attempt_cap", ctypes.c_uint32), ("round_cap", ctypes.c_uint32),
+                ("reject_attempts", ctypes.c_uint32), ("spin_limit", ctypes.c_uint32)]
+
+
+class fks_map_info_t(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("seed", ctypes.c_uint64), ("slots", ctypes.c_uint64),
+                ("slot_capacity", ctypes.c_uint64), ("bytes", ctypes.c_uint64),
+                ("attempts_sum", ctypes.c_uint64), ("context_bytes", ctypes.c_uint64),
+                ("round", ctypes.c_uint32), ("max_bucket", ctypes.c_uint32),
+                ("max_attempt", ctypes.c_uint32), ("key_kind", ctypes.c_uint32),
+                ("val_type", ctypes.c_uint32), ("overflow_partitions", ctypes.c_uint32),
+                ("nonempty_buckets", ctypes.c_uint64)]
+
+
+class fks_build_profile(ctypes.Structure):
+    _fields_ = [("fingerprint_ms", ctypes.c_float), ("count_ms", ctypes.c_float),
+                ("scan_ms", ctypes.c_float), ("scatter_ms", ctypes.c_float),
+                ("part_build_ms", ctypes.c_float), ("passes", ctypes.c_uint32)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libfks.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run `python -m paper_2508_11443_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, u64, u32, i64, st = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64, ctypes.c_int
+        L.fks_build_u64.argtypes = [vp, vp, ctypes.c_int, u64, u64, vp, vp, vp, ctypes.POINTER(vp)]
+        L.fks_build_bytes.argtypes = [vp, vp, vp, ctypes.c_int, u64, u64, vp, vp, vp, ctypes.POINTER(vp)]
+        L.fks_lookup_u64.argtypes = [vp, vp, u64, vp, vp, i64, vp]
+        L.fks_lookup_bytes.argtypes = [vp, vp, vp, u64, vp, vp, i64, vp]
+        L.fks_build_batched.argtypes = [ctypes.c_int, vp, vp, vp, vp, vp, u32, vp, ctypes.c_int, vp, vp,
+                                        vp, ctypes.POINTER(vp), vp]
+        L.fks_lookup_batched.argtypes = [vp, vp, vp, vp, vp, u64, vp, vp, i64, vp]
+        L.fks_mapset_size.argtypes = [vp]
+        L.fks_mapset_size.restype = u32
+        L.fks_mapset_get.argtypes = [vp, u32]
+        L.fks_mapset_get.restype = vp
+        L.fks_map_info.argtypes = [vp, ctypes.POINTER(fks_map_info_t)]
+        L.fks_map_export.argtypes = [vp, vp, vp, vp, vp]
+        L.fks_map_destroy.argtypes = [vp]
+        L.fks_map_destroy.restype = None
+        L.fks_mapset_destroy.argtypes = [vp]
+        L.fks_mapset_destroy.restype = None
+        L.fks_status_str.argtypes = [st]
+        L.fks_status_str.restype = ctypes.c_char_p
+        L.fks_last_error.argtypes = []
+        L.fks_last_error.restype = ctypes.c_char_p
+        L.fks_profile_enable.argtypes = [ctypes.c_int]
+        L.fks_profile_enable.restype = None
+        L.fks_last_build_profile.argtypes = [ctypes.POINTER(fks_build_profile)]
+        L.fks_last_build_profile.restype = st
+        L.fks_kernel_launches.argtypes = []
+        L.fks_kernel_launches.restype = u64
+        L.fks_test_hold_first_partition.argtypes = [ctypes.c_int]
+        L.fks_test_hold_first_partition.restype = None
+        for name in ("fks_build_u64", "fks_build_bytes", "fks_lookup_u64", "fks_lookup_bytes",
+                     "fks_build_batched", "fks_lookup_batched", "fks_map_info", "fks_map_export"):
+            getattr(L, name).restype = st
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != FKS_OK:
+        raise FksError(status, lib().fks_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _val_type(vals) -> int:
+    import torch
+    if vals.dtype == torch.int64:
+        return FKS_VAL_I64
+    if vals.dtype == torch.int32:
+        return FKS_VAL_I32
+    raise TypeError("values must be int32 or int64")
+
+
+def make_opts(**kw) -> fks_build_opts:
+    o = fks_build_opts()
+    o.struct_size = ctypes.sizeof(fks_build_opts)
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Map:
+    """Owning handle of a built map (destroyed with the object)."""
+
+    def __init__(self, handle: int, owner=None):
+        self.handle = handle
+        self._owner = owner  # a MapSet for borrowed handles
+
+    def info(self) -> fks_map_info_t:
+        return fks_map_info(self)
+
+    def __del__(self):
+        if self._owner is None and self.handle and _lib is not None:
+            _lib.fks_map_destroy(self.handle)
+            self.handle = None
+
+
+class MapSet:
+    def __init__(self, handle: int, status: np.ndarray):
+        self.handle = handle
+        self.status = status
+
+    def __len__(self):
+        return int(lib().fks_mapset_size(self.handle))
+
+    def get(self, j: int):
+        h = lib().fks_mapset_get(self.handle, j)
+        return Map(h, owner=self) if h else None
+
+    def __del__(self):
+        if self.handle and _lib is not None:
+            _lib.fks_mapset_destroy(self.handle)
+            self.handle = None
+
+
+def fks_build_u64(keys, vals, seed: int, opts: fks_build_opts | None = None, stream=None) -> Map:
+    h = ctypes.c_void_p()
+    n = keys.numel()
+    _check(lib().fks_build_u64(_ptr(keys), _ptr(vals), _val_type(vals), n, seed & (2**64 - 1),
+                               ctypes.byref(opts) if opts else None, None, _stream(stream),
+                               ctypes.byref(h)))
+    return Map(h.value)
+
+
+def fks_build_bytes(ctx, offs, vals, seed: int, opts: fks_build_opts | None = None,
+                    stream=None) -> Map:
+    h = ctypes.c_void_p()
+    n = offs.numel() - 1
+    _check(lib().fks_build_bytes(_ptr(ctx), _ptr(offs), _ptr(vals), _val_type(vals), n,
+                                 seed & (2**64 - 1), ctypes.byref(opts) if opts else None, None,
+                                 _stream(stream), ctypes.byref(h)))
+    return Map(h.value)
+
+
+def fks_lookup_u64(m: Map, q, out_vals=None, out_found=None, absent: int = -1, stream=None):
+    _check(lib().fks_lookup_u64(m.handle, _ptr(q), q.numel(), _ptr(out_vals), _ptr(out_found),
+                                absent, _stream(stream)))
+
+
+def fks_lookup_bytes(m: Map, qctx, qoffs, out_vals=None, out_found=None, absent: int = -1,
+                     stream=None):
+    _check(lib().fks_lookup_bytes(m.handle, _ptr(qctx), _ptr(qoffs), qoffs.numel() - 1,
+                                  _ptr(out_vals), _ptr(out_found), absent, _stream(stream)))
+
+
+def fks_build_batched(kind: int, keys, ctx, offs, seg: np.ndarray, seeds: np.ndarray, vals,
+                      opts: fks_build_opts | None = None, stream=None, raise_on_error=True) -> MapSet:
+    seg = np.ascontiguousarray(seg, np.int64)
+    seeds = np.ascontiguousarray(seeds, np.uint64)
+    m = seg.size - 1
+    status = np.zeros(m, np.int32)
+    h = ctypes.c_void_p()
+    st = lib().fks_build_batched(kind, _ptr(keys), _ptr(ctx), _ptr(offs),
+                                 seg.ctypes.data_as(ctypes.c_void_p),
+                                 seeds.ctypes.data_as(ctypes.c_void_p), m, _ptr(vals),
+                                 _val_type(vals), ctypes.byref(opts) if opts else None, None,
+                                 _stream(stream), ctypes.byref(h), status.ctypes.data_as(ctypes.c_void_p))
+    s = MapSet(h.value, status)
+    if raise_on_error or not h.value:
+        _check(st)
+    return s
+
+
+def fks_lookup_batched(s: MapSet, map_ids, q=None, qctx=None, qoffs=None, out_vals=None,
+                       out_found=None, absent: int = -1, stream=None):
+    nq = map_ids.numel()
+    _check(lib().fks_lookup_batched(s.handle, _ptr(map_ids), _ptr(q), _ptr(qctx), _ptr(qoffs), nq,
+                                    _ptr(out_vals), _ptr(out_found), absent, _stream(stream)))
+
+
+def fks_map_info(m: Map) -> fks_map_info_t:
+    info = fks_map_info_t()
+    _check(lib().fks_map_info(m.handle, ctypes.byref(info)))
+    return info
+
+
+def fks_map_export(m: Map, stream=None):
+    """(desc uint64[n], slots uint64[S, 2 or 4], ctx uint8[] or None) on the host."""
+    info = fks_map_info(m)
+    words = 4 if info.key_kind == FKS_KEY_BYTES else 2
+    desc = np.empty(info.n, np.uint64)
+    slots = np.empty((info.slots, words), np.uint64)
+    ctx = np.empty(max(info.context_bytes, 1), np.uint8) if info.key_kind == FKS_KEY_BYTES else None
+    _check(lib().fks_map_export(m.handle, desc.ctypes.data_as(ctypes.c_void_p),
+                                slots.ctypes.data_as(ctypes.c_void_p),
+                                None if ctx is None else ctx.ctypes.data_as(ctypes.c_void_p),
+                                _stream(stream)))
+    if ctx is not None:
+        ctx = ctx[: info.context_bytes]
+    return desc, slots, ctx
+
+
+def fks_status_str(status: int) -> str:
+    return lib().fks_status_str(status).decode()
+
+
+def fks_profile_enable(on: bool):
+    lib().fks_profile_enable(1 if on else 0)
+
+
+def fks_last_build_profile() -> fks_build_profile:
+    p = fks_build_profile()
+    _check(lib().fks_last_build_profile(ctypes.byref(p)))
+    return p
+
+
+def fks_kernel_launches() -> int:
+    return int(lib().fks_kernel_launches())
+
+
+def fks_test_hold_first_partition(on: bool):
+    lib().fks_test_hold_first_partition(1 if on else 0)
