@@ -9,6 +9,7 @@
 // A per-call build is the one-map case of the same code.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -88,6 +89,13 @@ static int sm_count() {
       uint64_t thr = UINT64_MAX;
       cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
     }
+    // Lookups are random 8 B / 16 B reads: ask L2 to fetch single 32-byte
+    // sectors on a miss instead of larger promoted blocks (a per-context
+    // hint that ends with the process; FKS_L2_FETCH overrides it).
+    size_t gran = 32;
+    if (const char* env = getenv("FKS_L2_FETCH")) gran = size_t(atoi(env));
+    if (gran) cudaDeviceSetLimit(cudaLimitMaxL2FetchGranularity, gran);
+    cudaGetLastError();
     if (sms <= 0) sms = 148;
   });
   return sms;
@@ -293,8 +301,8 @@ static fks_status build_impl(const BuildIn& in, const Opts& o, const Alloc& A, c
   const size_t s_ticket = cs.take<uint32_t>(4);
   const size_t s_ovl = cs.take<uint32_t>(P_all + 1);
   const size_t s_ove = cs.take<uint64_t>(P_all + 1);
-  const size_t s_skey = cs.take<uint64_t>(total);
-  const size_t s_spay = cs.take<uint64_t>(total * PW);
+  const size_t s_skey = cs.take<uint64_t>(total + 2);  // +2: 16-byte rounded bulk copies
+  const size_t s_spay = cs.take<uint64_t>((total + 2) * PW);
   const size_t s_maps = cs.take<MapDev>(m);
   const size_t s_pseg = cs.take<uint64_t>(m + 1);
   const size_t s_qseg = cs.take<uint32_t>(m + 1);

@@ -162,22 +162,39 @@ __global__ void __launch_bounds__(256) k_partition(PassDev p, int agg) {
   const uint64_t warp0 = (uint64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31u)) * kUnroll;
   const uint64_t stride = uint64_t(gridDim.x) * blockDim.x * kUnroll;
   const MapDev* maps = p.maps;
+  // the one-map case keeps its parameters in registers
+  const uint64_t kb0 = maps[0].key_begin, pb0 = maps[0].pass_begin;
+  const HashConsts c10 = maps[0].c1;
+  const uint32_t n0 = maps[0].n, part0 = maps[0].part_begin;
+  const uint64_t* __restrict__ hkeys = p.hkeys;
   for (uint64_t base = warp0; base < p.total; base += stride) {
-    uint64_t k[kUnroll], in[kUnroll];
+    uint64_t k[kUnroll], in[kUnroll], pv[kUnroll], po[kUnroll];
     uint32_t gp[kUnroll];
     bool ok[kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       const uint64_t e = base + uint64_t(u) * 32 + lane;
       ok[u] = e < p.total;
-      uint32_t j = 0;
-      if (ok[u] && p.m > 1) j = upper_seg(seg, p.m, e);
-      const uint64_t kb = maps[j].key_begin, pb = maps[j].pass_begin;
-      in[u] = kb + (e - pb);
-      k[u] = ok[u] ? __ldg(reinterpret_cast<const unsigned long long*>(p.hkeys) + in[u]) : 0;
-      const HashConsts c1 = maps[j].c1;
-      const uint32_t b = reduce32(hash32(c1, k[u]), maps[j].n);
-      gp[u] = maps[j].part_begin + (b >> kLogB);
+      pv[u] = po[u] = 0;
+      if (p.m == 1) {
+        in[u] = kb0 + (e - pb0);
+        k[u] = ok[u] ? __ldcs(reinterpret_cast<const unsigned long long*>(hkeys) + in[u]) : 0;
+        gp[u] = part0 + (reduce32(hash32(c10, k[u]), n0) >> kLogB);
+      } else {
+        const uint32_t j = ok[u] ? upper_seg(seg, p.m, e) : 0u;
+        in[u] = maps[j].key_begin + (e - maps[j].pass_begin);
+        k[u] = ok[u] ? __ldcs(reinterpret_cast<const unsigned long long*>(hkeys) + in[u]) : 0;
+        const HashConsts c1 = maps[j].c1;
+        gp[u] = maps[j].part_begin + (reduce32(hash32(c1, k[u]), maps[j].n) >> kLogB);
+      }
+      if (kScatter && ok[u]) {  // payload loads issued before the claims
+        pv[u] = uint64_t(load_val(p.vals, p.vals_i64, in[u]));
+        if (kStr) {
+          const int64_t o0 = __ldg(reinterpret_cast<const long long*>(p.offs) + in[u]);
+          const int64_t o1 = __ldg(reinterpret_cast<const long long*>(p.offs) + in[u] + 1);
+          po[u] = offlen_pack(uint64_t(o0), uint64_t(o1 - o0));
+        }
+      }
     }
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
@@ -187,15 +204,8 @@ __global__ void __launch_bounds__(256) k_partition(PassDev p, int agg) {
         const uint32_t pos = claim<true>(p.part_cursor, gp[u], ok[u], agg);
         if (ok[u]) {
           p.stage_key[pos] = k[u];
-          const int64_t v = load_val(p.vals, p.vals_i64, in[u]);
-          if (!kStr) {
-            p.stage_pay[pos] = uint64_t(v);
-          } else {
-            const int64_t o0 = __ldg(reinterpret_cast<const long long*>(p.offs) + in[u]);
-            const int64_t o1 = __ldg(reinterpret_cast<const long long*>(p.offs) + in[u] + 1);
-            reinterpret_cast<ulonglong2*>(p.stage_pay)[pos] =
-                make_ulonglong2(offlen_pack(uint64_t(o0), uint64_t(o1 - o0)), uint64_t(v));
-          }
+          if (!kStr) p.stage_pay[pos] = pv[u];
+          else reinterpret_cast<ulonglong2*>(p.stage_pay)[pos] = make_ulonglong2(po[u], pv[u]);
         }
       }
     }
@@ -244,20 +254,30 @@ __global__ void __launch_bounds__(1024) k_scan_parts(PassDev p) {
 }
 
 // -------------------------------------------------------------- partition CTA
+__host__ __device__ constexpr uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
+
+// Shared memory of a partition CTA.  raw*: the partition's staged keys and
+// payloads as delivered by the bulk-copy engine (the key range may start one
+// element early to keep the copy 16-byte aligned); g*: the same entries
+// grouped by bucket; owner: the partition's slot image as member indices.
 template <int PW>
 struct Smem {
-  static constexpr uint32_t kGkey = 0;
+  static constexpr uint32_t kRawN = kCap + 2;
+  static constexpr uint32_t kRawKey = 0;
+  static constexpr uint32_t kRawPay = align16(kRawKey + kRawN * 8);
+  static constexpr uint32_t kGkey = align16(kRawPay + kRawN * 8 * PW);
   static constexpr uint32_t kGpay = kGkey + kCap * 8;
   static constexpr uint32_t kOwner = kGpay + kCap * 8 * PW;
   static constexpr uint32_t kCnt = kOwner + kOwnerCap * 2;
   static constexpr uint32_t kGst = kCnt + kB * 4;
   static constexpr uint32_t kSoff = kGst + (kB + 4) * 4;
   static constexpr uint32_t kAtt = kSoff + kB * 4;
-  static constexpr uint32_t kBytes = kAtt + kB * 2;
+  static constexpr uint32_t kBytes = align16(kAtt + kB * 2);
 };
 
 struct PartCtl {
-  uint32_t gp, j, skip, nbig, maxs, maxatt, flag_a, flag_b, nonempty;
+  uint32_t gp, skip, nbig, maxs, maxatt, flag_a, flag_b, nonempty;
+  uint32_t next_gp, next_issued, abort;
   uint64_t excl, Spart, attsum;
   unsigned long long fillmin;  // (slot << 32) | member of a CTA-searched bucket
   uint32_t wsum[kPartThreads / 32];
@@ -285,22 +305,63 @@ __device__ __forceinline__ MapRegs load_map(const PassDev& p, uint32_t j) {
   return r;
 }
 
-// Hist of the partition's buckets + exclusive Presum of s and s^2.
-// Leaves cnt[] holding s, gst[] the group starts (gst[kB] = keys), soff[] the
-// partition-local slot offsets, and ctl.Spart = sum s^2.
+// ---- bulk copies into shared memory, completion on an mbarrier
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Thread 0: start the copy of partition gp's staged range into raw*.
+// Returns 1 if a copy was issued (the caller waits on the mbarrier).
 template <int PW>
-__device__ void count_and_scan(const PassDev& p, const MapRegs& M, uint32_t b0, uint64_t e0,
-                               uint64_t e1, uint32_t* cnt, uint32_t* gst, uint32_t* soff,
-                               PartCtl& ctl) {
+__device__ uint32_t issue_stage(const PassDev& p, uint32_t gp, uint64_t* raw_key, uint64_t* raw_pay,
+                                uint64_t* bar) {
+  if (gp >= p.P) return 0;
+  const uint64_t e0 = p.part_start[gp], e1 = p.part_start[gp + 1];
+  if (e1 == e0 || e1 - e0 > kCap) return 0;
+  const uint64_t a0 = e0 & ~1ull;                 // 16-byte aligned start of the key copy
+  const uint32_t nk = uint32_t((e1 - a0 + 1) & ~1ull);  // even element count
+  const uint32_t bk = nk * 8u;
+  const uint32_t bp = PW == 1 ? bk : uint32_t(e1 - e0) * 16u;
+  const uint64_t* sp = PW == 1 ? p.stage_pay + a0 : p.stage_pay + 2 * e0;
+  fence_proxy_async_smem();
+  mbar_expect_tx(bar, bk + bp);
+  bulk_g2s(raw_key, p.stage_key + a0, bk, bar);
+  bulk_g2s(raw_pay, sp, bp, bar);
+  return 1;
+}
+
+// Exclusive Presum of s and s^2 over the partition's buckets (cnt[] holds s).
+// Leaves gst[] the group starts (gst[kB] = keys), soff[] the partition-local
+// slot offsets, ctl.Spart = sum s^2, ctl.maxs, ctl.nonempty.
+__device__ void scan_buckets(const uint32_t* cnt, uint32_t* gst, uint32_t* soff, PartCtl& ctl) {
   const uint32_t t = threadIdx.x;
-  for (uint32_t i = t; i < kB; i += kPartThreads) cnt[i] = 0;
-  __syncthreads();
-  for (uint64_t e = e0 + t; e < e1; e += kPartThreads) {
-    const uint64_t k = p.stage_key[e];
-    const uint32_t lb = reduce32(hash32(M.c1, k), M.n) - b0;
-    atomicAdd(cnt + lb, 1u);
-  }
-  __syncthreads();
   constexpr uint32_t kPer = kB / kPartThreads;
   uint32_t c[kPer], ls = 0, mx = 0, ne = 0;
   uint64_t ls2 = 0;
@@ -312,8 +373,6 @@ __device__ void count_and_scan(const PassDev& p, const MapRegs& M, uint32_t b0, 
     mx = max(mx, c[i]);
     ne += c[i] != 0;
   }
-  ne = __reduce_add_sync(0xFFFFFFFFu, ne);
-  if (lane_id() == 0) atomicAdd(&ctl.nonempty, ne);
   uint32_t inc = ls;
   uint64_t inc2 = ls2;
   for (int d = 1; d < 32; d <<= 1) {
@@ -324,12 +383,16 @@ __device__ void count_and_scan(const PassDev& p, const MapRegs& M, uint32_t b0, 
       inc2 += x2;
     }
   }
-  for (int d = 16; d > 0; d >>= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, d));
+  mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+  ne = __reduce_add_sync(0xFFFFFFFFu, ne);
   if (lane_id() == 31) {
     ctl.wsum[t >> 5] = inc;
     ctl.wsum2[t >> 5] = inc2;
   }
-  if (lane_id() == 0) atomicMax(&ctl.maxs, mx);
+  if (lane_id() == 0) {
+    atomicMax(&ctl.maxs, mx);
+    atomicAdd(&ctl.nonempty, ne);
+  }
   __syncthreads();
   uint32_t we = 0;
   uint64_t we2 = 0;
@@ -353,35 +416,59 @@ __device__ void count_and_scan(const PassDev& p, const MapRegs& M, uint32_t b0, 
   __syncthreads();
 }
 
-// Decoupled look-back (thread 0): exclusive slot prefix of partition gp within
-// its map.  Every wait is bounded by cfg.spin_limit polls.
-__device__ uint64_t look_back(const PassDev& p, uint32_t gp, uint32_t first, uint64_t agg,
-                              bool* timed_out) {
+// Hist of a partition's buckets straight from global memory (overflow path).
+__device__ __noinline__ void count_global(const PassDev& p, const MapRegs& M, uint32_t b0, uint64_t e0,
+                                          uint64_t e1, uint32_t* cnt) {
+  for (uint64_t e = e0 + threadIdx.x; e < e1; e += kPartThreads) {
+    const uint64_t k = p.stage_key[e];
+    atomicAdd(cnt + (reduce32(hash32(M.c1, k), M.n) - b0), 1u);
+  }
+}
+
+// Decoupled look-back by one warp: exclusive slot prefix of partition gp
+// within its map, 32 predecessors per step.  Every wait is bounded.
+__device__ uint64_t look_back_warp(const PassDev& p, uint32_t gp, uint32_t first, uint64_t agg,
+                                   bool* timed_out) {
+  const uint32_t lane = lane_id();
   const bool hold = p.cfg.hold_first && gp == 0;
+  *timed_out = false;
   if (gp == first) {
-    if (!hold) st_relaxed(p.lookback + gp, kLbFlagP | sat(agg));
+    if (lane == 0 && !hold) st_relaxed(p.lookback + gp, kLbFlagP | sat(agg));
     return 0;
   }
-  if (!hold) st_relaxed(p.lookback + gp, kLbFlagA | sat(agg));
+  if (lane == 0 && !hold) st_relaxed(p.lookback + gp, kLbFlagA | sat(agg));
   uint64_t excl = 0;
-  uint32_t q = gp - 1, polls = 0, ns = 32;
+  int64_t hi = int64_t(gp) - 1;
+  uint32_t polls = 0, ns = 32;
   for (;;) {
-    const uint64_t w = ld_relaxed(p.lookback + q);
-    if (w == 0) {
+    const int64_t q = hi - int64_t(lane);
+    const bool real = q >= int64_t(first);
+    uint64_t w = real ? ld_relaxed(p.lookback + q) : kLbFlagP;
+    bool to = false;
+    while (__any_sync(0xFFFFFFFFu, w == 0)) {
       if (++polls > p.cfg.spin_limit) {
-        *timed_out = true;
-        excl = kSat;
+        to = true;
         break;
       }
       __nanosleep(ns);
       if (ns < 1024) ns <<= 1;
-      continue;
+      if (w == 0) w = ld_relaxed(p.lookback + q);
     }
-    excl = sat(excl + (w & kLbVal));
-    if ((w >> 62) == 2 || q == first) break;
-    --q;
+    if (to) {
+      *timed_out = true;
+      excl = kSat;
+      break;
+    }
+    const uint32_t pm = __ballot_sync(0xFFFFFFFFu, (w >> 62) == 2);
+    const uint32_t upto = pm ? uint32_t(__ffs(pm) - 1) : 31u;
+    uint64_t v = lane <= upto ? (w & kLbVal) : 0ull;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, d);
+    excl = sat(excl + v);
+    if (pm) break;
+    hi -= 32;
   }
-  if (!hold) st_relaxed(p.lookback + gp, kLbFlagP | sat(excl + agg));
+  if (lane == 0 && !hold) st_relaxed(p.lookback + gp, kLbFlagP | sat(excl + agg));
   return excl;
 }
 
@@ -470,8 +557,7 @@ __device__ void place_thread(const PassDev& p, const uint64_t* k, const uint64_t
     for (uint32_t t = 0; t < m; ++t)
       if (owner[so + t] == kOwnerEmpty) owner[so + t] = uint16_t(kOwnerFill | (g0 + xmin));
   } else {
-    if (s > 1)
-      for (uint32_t t = 0; t < m; ++t) write_slot<PW>(p, slot0 + t, k[xmin], gpay + PW * (g0 + xmin), true);
+    for (uint32_t t = 0; t < m; ++t) write_slot<PW>(p, slot0 + t, k[xmin], gpay + PW * (g0 + xmin), true);
     for (uint32_t x = 0; x < s; ++x)
       write_slot<PW>(p, slot0 + reduce32(hash32(c, k[x]), m), k[x], gpay + PW * (g0 + x), false);
   }
@@ -479,10 +565,11 @@ __device__ void place_thread(const PassDev& p, const uint64_t* k, const uint64_t
 
 // make_2 + placement for a bucket larger than kThreadSearchMax, by the CTA.
 template <int PW>
-__device__ void search_place_cta(const PassDev& p, const uint64_t* k, const uint64_t* gpay,
-                                 uint32_t g0, uint32_t s, uint64_t seed, uint32_t round,
-                                 uint32_t b, uint16_t* owner, uint32_t so, uint64_t slot0,
-                                 bool owner_mode, uint32_t j, PartCtl& ctl, uint16_t* att_out) {
+__device__ __noinline__ void search_place_cta(const PassDev& p, const uint64_t* k, const uint64_t* gpay,
+                                              uint32_t g0, uint32_t s, uint64_t seed, uint32_t round,
+                                              uint32_t b, uint16_t* owner, uint32_t so, uint64_t slot0,
+                                              bool owner_mode, uint32_t j, PartCtl& ctl,
+                                              uint16_t* att_out) {
   const uint32_t t = threadIdx.x, m = s * s;
   int found = kSearchNext;
   for (uint32_t a = 0; a < p.cfg.attempt_cap; ++a) {
@@ -504,7 +591,7 @@ __device__ void search_place_cta(const PassDev& p, const uint64_t* k, const uint
     const HashConsts c = derive(seed, round, b, a);
     if (t == 0) ctl.flag_a = 0;
     __syncthreads();
-    for (uint32_t x = t; x < s && !ctl.flag_a; x += kPartThreads) {
+    for (uint32_t x = t; x < s; x += kPartThreads) {
       const uint32_t jx = reduce32(hash32(c, k[x]), m);
       for (uint32_t y = 0; y < s; ++y)
         if (y != x && reduce32(hash32(c, k[y]), m) == jx) {
@@ -534,7 +621,6 @@ __device__ void search_place_cta(const PassDev& p, const uint64_t* k, const uint
     ctl.attsum += uint64_t(found);
   }
   __syncthreads();
-  // filler = member with the lowest slot
   for (uint32_t x = t; x < s; x += kPartThreads) {
     const uint32_t jx = reduce32(hash32(c, k[x]), m);
     atomicMin(&ctl.fillmin, (static_cast<unsigned long long>(jx) << 32) | x);
@@ -556,37 +642,18 @@ __device__ void search_place_cta(const PassDev& p, const uint64_t* k, const uint
   __syncthreads();
 }
 
-// Groupby, level-two search, descriptors and slots of one partition whose
-// counts/scan are already in shared memory.  gkey/gpay point at the grouped
-// buffer (shared memory, or global memory for an overflow partition).
+// Level-two search (make_2) of every bucket of a grouped partition, then the
+// placement of its keys: slot image in shared memory (owner mode) or direct
+// writes.  Buckets above kThreadSearchMax keys are done by the whole CTA.
 template <int PW>
-__device__ void group_search_write(const PassDev& p, const MapRegs& M, uint32_t j, uint32_t b0,
-                                   uint32_t nb, uint64_t e0, uint64_t e1, uint64_t excl,
-                                   uint64_t* gkey, uint64_t* gpay, uint16_t* owner, uint32_t* cnt,
-                                   const uint32_t* gst, const uint32_t* soff, uint16_t* att,
-                                   PartCtl& ctl) {
-  const uint32_t t = threadIdx.x;
-  const uint64_t Sp = ctl.Spart;
-  const bool owner_mode = Sp <= kOwnerCap;
-  for (uint32_t i = t; i < kB; i += kPartThreads) cnt[i] = gst[i];
-  if (owner_mode)
-    for (uint32_t q = t; q < uint32_t(Sp); q += kPartThreads) owner[q] = kOwnerEmpty;
-  if (t == 0) ctl.nbig = 0;
-  __syncthreads();
-  // Groupby: scatter the partition's keys to their bucket's group.
-  for (uint64_t e = e0 + t; e < e1; e += kPartThreads) {
-    const uint64_t k = p.stage_key[e];
-    const uint32_t lb = reduce32(hash32(M.c1, k), M.n) - b0;
-    const uint32_t pos = atomicAdd(cnt + lb, 1u);
-    gkey[pos] = k;
-#pragma unroll
-    for (int w = 0; w < PW; ++w) gpay[PW * pos + w] = p.stage_pay[PW * e + w];
-  }
-  __syncthreads();
-  const uint64_t slot_part = M.slot_base + excl;  // slot index of partition-local slot 0
+__device__ void search_partition(const PassDev& p, const MapRegs& M, uint32_t j, uint32_t b0,
+                                 uint32_t nb, uint64_t slot_part, bool owner_mode,
+                                 const uint64_t* gkey, const uint64_t* gpay, uint16_t* owner,
+                                 const uint32_t* gst, const uint32_t* soff, uint16_t* att,
+                                 PartCtl& ctl) {
   uint32_t my_max = 0;
   uint64_t my_sum = 0;
-  for (uint32_t lb = t; lb < nb; lb += kPartThreads) {
+  for (uint32_t lb = threadIdx.x; lb < nb; lb += kPartThreads) {
     const uint32_t g0 = gst[lb], s = gst[lb + 1] - g0;
     uint16_t a_out = 0;
     if (s == 1) {
@@ -607,7 +674,7 @@ __device__ void group_search_write(const PassDev& p, const MapRegs& M, uint32_t 
         atomicExch(&p.status[j].next_round, 1u);
       }
     } else if (s > kThreadSearchMax) {
-      atomicAdd(&ctl.nbig, 1u);  // searched below by the whole CTA
+      atomicAdd(&ctl.nbig, 1u);
     }
     att[lb] = a_out;
   }
@@ -623,13 +690,22 @@ __device__ void group_search_write(const PassDev& p, const MapRegs& M, uint32_t 
     }
   }
   __syncthreads();
-  // descriptors of the partition's buckets (coalesced)
+}
+
+// Descriptors of the partition's buckets and, in owner mode, its slot image
+// (both coalesced).
+template <int PW>
+__device__ void write_partition(const PassDev& p, const MapRegs& M, uint32_t b0, uint32_t nb,
+                                uint64_t excl, bool owner_mode, const uint64_t* gkey,
+                                const uint64_t* gpay, const uint16_t* owner, const uint32_t* gst,
+                                const uint32_t* soff, const uint16_t* att, uint64_t Sp) {
+  const uint32_t t = threadIdx.x;
   for (uint32_t lb = t; lb < nb; lb += kPartThreads) {
     const uint32_t s = gst[lb + 1] - gst[lb];
     p.desc[M.desc_base + b0 + lb] = desc_pack(uint32_t(excl + soff[lb]), s, att[lb]);
   }
-  // slot image (coalesced)
   if (owner_mode) {
+    const uint64_t slot_part = M.slot_base + excl;
     for (uint32_t q = t; q < uint32_t(Sp); q += kPartThreads) {
       const uint16_t o = owner[q];
       const uint32_t idx = o & 0x7FFFu;
@@ -638,10 +714,21 @@ __device__ void group_search_write(const PassDev& p, const MapRegs& M, uint32_t 
   }
 }
 
+__device__ __forceinline__ void flush_stats(const PassDev& p, uint32_t j, const PartCtl& ctl) {
+  if (ctl.maxatt) atomicMax(&p.status[j].max_att, ctl.maxatt);
+  if (ctl.attsum)
+    atomicAdd(reinterpret_cast<unsigned long long*>(&p.status[j].att_sum), (unsigned long long)ctl.attsum);
+}
+
+// The partition CTA: a persistent loop over a ticketed queue of partitions.
+// While partition i is searched and written, the bulk-copy engine already
+// stages partition i+1 into shared memory.
 template <int PW>
-__global__ void __launch_bounds__(kPartThreads) k_part_build(PassDev p) {
-  extern __shared__ __align__(16) uint8_t smem[];
+__global__ void __launch_bounds__(kPartThreads, PW == 1 ? 2 : 1) k_part_build(PassDev p) {
+  extern __shared__ __align__(128) uint8_t smem[];
   using L = Smem<PW>;
+  uint64_t* raw_key = reinterpret_cast<uint64_t*>(smem + L::kRawKey);
+  uint64_t* raw_pay = reinterpret_cast<uint64_t*>(smem + L::kRawPay);
   uint64_t* gkey = reinterpret_cast<uint64_t*>(smem + L::kGkey);
   uint64_t* gpay = reinterpret_cast<uint64_t*>(smem + L::kGpay);
   uint16_t* owner = reinterpret_cast<uint16_t*>(smem + L::kOwner);
@@ -650,65 +737,141 @@ __global__ void __launch_bounds__(kPartThreads) k_part_build(PassDev p) {
   uint32_t* soff = reinterpret_cast<uint32_t*>(smem + L::kSoff);
   uint16_t* att = reinterpret_cast<uint16_t*>(smem + L::kAtt);
   __shared__ PartCtl ctl;
+  __shared__ __align__(8) uint64_t bar;
   const uint32_t t = threadIdx.x;
+  constexpr uint32_t kPerThread = kCap / kPartThreads;
+  uint32_t parity = 0;
+  if (t == 0) {
+    mbar_init(&bar, 1);
+    ctl.abort = 0;
+    ctl.next_gp = atomicAdd(p.ticket, 1u);
+    ctl.next_issued = issue_stage<PW>(p, ctl.next_gp, raw_key, raw_pay, &bar);
+  }
+  __syncthreads();
   for (;;) {
-    __syncthreads();
-    if (t == 0) {
-      ctl.gp = atomicAdd(p.ticket, 1u);
-      ctl.nonempty = 0;
-      ctl.maxs = 0;
-      ctl.maxatt = 0;
-      ctl.attsum = 0;
-    }
-    __syncthreads();
-    const uint32_t gp = ctl.gp;
-    if (gp >= p.P) return;
+    const uint32_t gp = ctl.next_gp;
+    const uint32_t issued = ctl.next_issued;
+    if (gp >= p.P || ctl.abort) break;
     const uint32_t j = p.m == 1 ? 0u : upper_seg(p.part_seg, p.m, gp);
     const MapRegs M = load_map(p, j);
     const uint32_t b0 = (gp - M.part_begin) << kLogB;
     const uint32_t nb = min(kB, M.n - b0);
     const uint64_t e0 = p.part_start[gp], e1 = p.part_start[gp + 1];
-    count_and_scan<PW>(p, M, b0, e0, e1, cnt, gst, soff, ctl);
+    const uint32_t ne = uint32_t(e1 - e0 < 0xFFFFFFFFull ? e1 - e0 : 0xFFFFFFFFull);
+    for (uint32_t i = t; i < kB; i += kPartThreads) cnt[i] = 0;
     if (t == 0) {
-      bool to = false;
-      const uint64_t excl = look_back(p, gp, M.part_begin, ctl.Spart, &to);
-      ctl.excl = excl;
-      const uint64_t incl = excl + ctl.Spart;
-      ctl.skip = (to || incl > M.slot_cap) ? 1u : 0u;
-      if (to) atomicExch(&p.status[j].timeout, 1u);
-      if (incl > M.slot_cap) atomicExch(&p.status[j].reseed, 1u);
-      if (gp + 1 == M.part_end) p.status[j].S = incl;
-      atomicMax(&p.status[j].max_s, ctl.maxs);
-      atomicAdd(reinterpret_cast<unsigned long long*>(&p.status[j].nonempty),
-                (unsigned long long)ctl.nonempty);
+      ctl.maxs = ctl.maxatt = ctl.nonempty = ctl.nbig = 0;
+      ctl.attsum = 0;
+    }
+    if (issued) {  // bounded wait for the staged copy
+      uint32_t polls = 0;
+      while (!mbar_try_wait(&bar, parity)) {
+        if (++polls > p.cfg.spin_limit) {
+          ctl.abort = 1;
+          break;
+        }
+      }
+      parity ^= 1u;
     }
     __syncthreads();
-    if (ctl.skip) continue;
-    if (e1 - e0 > kCap) {
+    if (ctl.abort) {
+      if (t == 0) atomicExch(&p.status[j].timeout, 1u);
+      break;
+    }
+    const bool overflow = ne > kCap;
+    const uint32_t shift = uint32_t(e0 & 1ull);  // raw key index of element e0
+    uint16_t lbr[kPerThread], rk[kPerThread];
+    if (!overflow) {
+      // Hist of the partition's buckets from shared memory; the atomic's
+      // return value is the key's rank within its bucket.
+#pragma unroll
+      for (uint32_t u = 0; u < kPerThread; ++u) {
+        const uint32_t i = t + u * kPartThreads;
+        if (i < ne) {
+          const uint64_t k = raw_key[shift + i];
+          const uint32_t lb = reduce32(hash32(M.c1, k), M.n) - b0;
+          lbr[u] = uint16_t(lb);
+          rk[u] = uint16_t(atomicAdd(cnt + lb, 1u));
+        }
+      }
+    } else {
+      count_global(p, M, b0, e0, e1, cnt);
+    }
+    __syncthreads();
+    scan_buckets(cnt, gst, soff, ctl);
+    const uint64_t Sp = ctl.Spart;
+    const bool owner_mode = Sp <= kOwnerCap;
+    // warp 0: slot prefix of this partition (look-back); the other warps
+    // group the keys meanwhile
+    if (t < 32) {
+      bool to = false;
+      const uint64_t excl = look_back_warp(p, gp, M.part_begin, Sp, &to);
+      if (t == 0) {
+        const uint64_t incl = excl + Sp;
+        ctl.excl = excl;
+        ctl.skip = (to || incl > M.slot_cap) ? 1u : 0u;
+        if (to) atomicExch(&p.status[j].timeout, 1u);
+        if (incl > M.slot_cap) atomicExch(&p.status[j].reseed, 1u);
+        if (gp + 1 == M.part_end) p.status[j].S = incl;
+        atomicMax(&p.status[j].max_s, ctl.maxs);
+        atomicAdd(reinterpret_cast<unsigned long long*>(&p.status[j].nonempty),
+                  (unsigned long long)ctl.nonempty);
+      }
+    }
+    if (!overflow) {
+#pragma unroll
+      for (uint32_t u = 0; u < kPerThread; ++u) {
+        const uint32_t i = t + u * kPartThreads;
+        if (i < ne) {
+          const uint32_t pos = gst[lbr[u]] + rk[u];
+          gkey[pos] = raw_key[shift + i];
+#pragma unroll
+          for (int w = 0; w < PW; ++w) gpay[PW * pos + w] = raw_pay[PW * ((PW == 1 ? shift : 0) + i) + w];
+        }
+      }
+      if (owner_mode)
+        for (uint32_t q = t; q < uint32_t(Sp); q += kPartThreads) owner[q] = kOwnerEmpty;
+    }
+    __syncthreads();
+    // raw* is free again: stage the next partition while this one is searched
+    if (t == 0) {
+      ctl.next_gp = atomicAdd(p.ticket, 1u);
+      ctl.next_issued = issue_stage<PW>(p, ctl.next_gp, raw_key, raw_pay, &bar);
+    }
+    if (ctl.skip) {
+      __syncthreads();
+      continue;
+    }
+    if (overflow) {
       if (t == 0) {
         const uint32_t slot = atomicAdd(p.ovf_count, 1u);
         p.ovf_list[slot] = gp;
         p.ovf_excl[slot] = ctl.excl;
         atomicAdd(&p.status[j].overflow, 1u);
       }
+      __syncthreads();
       continue;
     }
-    group_search_write<PW>(p, M, j, b0, nb, e0, e1, ctl.excl, gkey, gpay, owner, cnt, gst, soff,
-                           att, ctl);
+    search_partition<PW>(p, M, j, b0, nb, M.slot_base + ctl.excl, owner_mode, gkey, gpay, owner, gst,
+                         soff, att, ctl);
+    write_partition<PW>(p, M, b0, nb, ctl.excl, owner_mode, gkey, gpay, owner, gst, soff, att, Sp);
+    if (t == 0) flush_stats(p, j, ctl);
     __syncthreads();
-    if (t == 0) {
-      if (ctl.maxatt) atomicMax(&p.status[j].max_att, ctl.maxatt);
-      if (ctl.attsum) atomicAdd(reinterpret_cast<unsigned long long*>(&p.status[j].att_sum),
-                                (unsigned long long)ctl.attsum);
+  }
+  // never leave with a bulk copy in flight
+  if (t == 0 && ctl.next_issued && ctl.abort) {
+    uint32_t polls = 0;
+    while (!mbar_try_wait(&bar, parity) && ++polls < p.cfg.spin_limit) {
     }
   }
 }
 
 // Partitions deferred because they hold more than kCap keys: grouped through
-// global memory (the rare, adversarial case).
+// global memory (the rare, adversarial case).  Group indices are
+// partition-local; the grouped buffer starts at the partition's first element.
 template <int PW>
-__global__ void __launch_bounds__(kPartThreads) k_part_overflow(PassDev p) {
-  extern __shared__ __align__(16) uint8_t smem[];
+__global__ void __launch_bounds__(kPartThreads, 1) k_part_overflow(PassDev p) {
+  extern __shared__ __align__(128) uint8_t smem[];
   using L = Smem<PW>;
   uint16_t* owner = reinterpret_cast<uint16_t*>(smem + L::kOwner);
   uint32_t* cnt = reinterpret_cast<uint32_t*>(smem + L::kCnt);
@@ -718,29 +881,42 @@ __global__ void __launch_bounds__(kPartThreads) k_part_overflow(PassDev p) {
   __shared__ PartCtl ctl;
   const uint32_t t = threadIdx.x;
   const uint32_t gp = p.ovf_list[blockIdx.x];
-  if (t == 0) {
-    ctl.maxs = 0;
-    ctl.maxatt = 0;
-    ctl.attsum = 0;
-    ctl.nonempty = 0;
-  }
-  __syncthreads();
   const uint32_t j = p.m == 1 ? 0u : upper_seg(p.part_seg, p.m, gp);
   const MapRegs M = load_map(p, j);
   const uint32_t b0 = (gp - M.part_begin) << kLogB;
   const uint32_t nb = min(kB, M.n - b0);
   const uint64_t e0 = p.part_start[gp], e1 = p.part_start[gp + 1];
-  count_and_scan<PW>(p, M, b0, e0, e1, cnt, gst, soff, ctl);
   const uint64_t excl = p.ovf_excl[blockIdx.x];
-  // group indices are partition-local; the grouped buffer starts at e0
-  group_search_write<PW>(p, M, j, b0, nb, e0, e1, excl, p.ovf_key + e0, p.ovf_pay + PW * e0,
-                         owner, cnt, gst, soff, att, ctl);
-  __syncthreads();
+  uint64_t* gkey = p.ovf_key + e0;
+  uint64_t* gpay = p.ovf_pay + PW * e0;
+  for (uint32_t i = t; i < kB; i += kPartThreads) cnt[i] = 0;
   if (t == 0) {
-    if (ctl.maxatt) atomicMax(&p.status[j].max_att, ctl.maxatt);
-    if (ctl.attsum) atomicAdd(reinterpret_cast<unsigned long long*>(&p.status[j].att_sum),
-                              (unsigned long long)ctl.attsum);
+    ctl.maxs = ctl.maxatt = ctl.nonempty = ctl.nbig = 0;
+    ctl.attsum = 0;
   }
+  __syncthreads();
+  count_global(p, M, b0, e0, e1, cnt);
+  __syncthreads();
+  scan_buckets(cnt, gst, soff, ctl);
+  const uint64_t Sp = ctl.Spart;
+  const bool owner_mode = Sp <= kOwnerCap;
+  for (uint32_t i = t; i < kB; i += kPartThreads) cnt[i] = gst[i];
+  if (owner_mode)
+    for (uint32_t q = t; q < uint32_t(Sp); q += kPartThreads) owner[q] = kOwnerEmpty;
+  __syncthreads();
+  for (uint64_t e = e0 + t; e < e1; e += kPartThreads) {
+    const uint64_t k = p.stage_key[e];
+    const uint32_t lb = reduce32(hash32(M.c1, k), M.n) - b0;
+    const uint32_t pos = atomicAdd(cnt + lb, 1u);
+    gkey[pos] = k;
+#pragma unroll
+    for (int w = 0; w < PW; ++w) gpay[PW * pos + w] = p.stage_pay[PW * e + w];
+  }
+  __syncthreads();
+  search_partition<PW>(p, M, j, b0, nb, M.slot_base + excl, owner_mode, gkey, gpay, owner, gst, soff,
+                       att, ctl);
+  write_partition<PW>(p, M, b0, nb, excl, owner_mode, gkey, gpay, owner, gst, soff, att, Sp);
+  if (t == 0) flush_stats(p, j, ctl);
 }
 
 // -------------------------------------------------------------- duplicate test

@@ -15,7 +15,7 @@ constexpr int kLogB = 10;
 constexpr uint32_t kB = 1u << kLogB;
 constexpr uint32_t kCap = 2048;        // keys of a partition held in shared memory
 constexpr uint32_t kOwnerCap = 4096;   // slots of a partition staged in shared memory
-constexpr int kPartThreads = 256;      // threads of a partition CTA
+constexpr int kPartThreads = 512;      // threads of a partition CTA
 constexpr uint32_t kThreadSearchMax = 64;  // larger buckets are searched by the whole CTA
 constexpr uint16_t kOwnerEmpty = 0xFFFF;
 constexpr uint16_t kOwnerFill = 0x8000;

@@ -108,7 +108,7 @@ def test_lookup_edge_shapes(F):
     # empty batch is a no-op
     F.fks_lookup_u64(gm, u64(np.zeros(0, np.uint64)), None, None)
     # unaligned needles / outputs (scalar path), ragged length
-    qt = u64(np.concatenate([[0], w.queries]))[1:]
+    qt = u64(np.concatenate([np.zeros(1, np.uint64), w.queries]))[1:]
     out = torch.empty(len(w.queries) + 1, dtype=torch.int64, device="cuda")[1:]
     found = torch.empty(len(w.queries) + 3, dtype=torch.uint8, device="cuda")[3:]
     F.fks_lookup_u64(gm, qt, out, found, -1)
