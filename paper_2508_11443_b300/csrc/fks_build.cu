@@ -192,7 +192,9 @@ __global__ void __launch_bounds__(256) k_partition(PassDev p, int agg) {
         if (kStr) {
           const int64_t o0 = __ldg(reinterpret_cast<const long long*>(p.offs) + in[u]);
           const int64_t o1 = __ldg(reinterpret_cast<const long long*>(p.offs) + in[u] + 1);
-          po[u] = offlen_pack(uint64_t(o0), uint64_t(o1 - o0));
+          const bool valid = o0 >= 0 && o1 >= o0 && o1 - o0 < (int64_t(1) << 24) && o1 < (int64_t(1) << 40);
+          // invalid offsets (the map fails with INVALID_ARG) become an empty slice
+          po[u] = valid ? offlen_pack(uint64_t(o0), uint64_t(o1 - o0)) : 0ull;
         }
       }
     }
@@ -277,6 +279,7 @@ struct Smem {
 
 struct PartCtl {
   uint32_t gp, skip, nbig, maxs, maxatt, flag_a, flag_b, nonempty;
+  uint32_t failed;  // a bucket found no constants: this pass of the map is discarded
   uint32_t next_gp, next_issued, abort;
   uint64_t excl, Spart, attsum;
   unsigned long long fillmin;  // (slot << 32) | member of a CTA-searched bucket
@@ -609,6 +612,7 @@ __device__ __noinline__ void search_place_cta(const PassDev& p, const uint64_t* 
       if (found == kSearchDup) atomicExch(&p.status[j].dup, 1u);
       else atomicExch(&p.status[j].next_round, 1u);
       *att_out = 0;
+      ctl.failed = 1;
     }
     __syncthreads();
     return;
@@ -668,10 +672,9 @@ __device__ void search_partition(const PassDev& p, const MapRegs& M, uint32_t j,
         const HashConsts c = derive(M.seed, M.round, b0 + lb, uint32_t(a));
         place_thread<PW>(p, gkey + g0, gpay, g0, s, c, owner, soff[lb], slot_part + soff[lb],
                          owner_mode);
-      } else if (a == kSearchDup) {
-        atomicExch(&p.status[j].dup, 1u);
       } else {
-        atomicExch(&p.status[j].next_round, 1u);
+        atomicExch(a == kSearchDup ? &p.status[j].dup : &p.status[j].next_round, 1u);
+        ctl.failed = 1;
       }
     } else if (s > kThreadSearchMax) {
       atomicAdd(&ctl.nbig, 1u);
@@ -708,6 +711,7 @@ __device__ void write_partition(const PassDev& p, const MapRegs& M, uint32_t b0,
     const uint64_t slot_part = M.slot_base + excl;
     for (uint32_t q = t; q < uint32_t(Sp); q += kPartThreads) {
       const uint16_t o = owner[q];
+      if (o == kOwnerEmpty) continue;  // only when a bucket failed (never written then)
       const uint32_t idx = o & 0x7FFFu;
       write_slot<PW>(p, slot_part + q, gkey[idx], gpay + PW * idx, (o & kOwnerFill) != 0);
     }
@@ -760,7 +764,7 @@ __global__ void __launch_bounds__(kPartThreads, PW == 1 ? 2 : 1) k_part_build(Pa
     const uint32_t ne = uint32_t(e1 - e0 < 0xFFFFFFFFull ? e1 - e0 : 0xFFFFFFFFull);
     for (uint32_t i = t; i < kB; i += kPartThreads) cnt[i] = 0;
     if (t == 0) {
-      ctl.maxs = ctl.maxatt = ctl.nonempty = ctl.nbig = 0;
+      ctl.maxs = ctl.maxatt = ctl.nonempty = ctl.nbig = ctl.failed = 0;
       ctl.attsum = 0;
     }
     if (issued) {  // bounded wait for the staged copy
@@ -854,7 +858,8 @@ __global__ void __launch_bounds__(kPartThreads, PW == 1 ? 2 : 1) k_part_build(Pa
     }
     search_partition<PW>(p, M, j, b0, nb, M.slot_base + ctl.excl, owner_mode, gkey, gpay, owner, gst,
                          soff, att, ctl);
-    write_partition<PW>(p, M, b0, nb, ctl.excl, owner_mode, gkey, gpay, owner, gst, soff, att, Sp);
+    if (!ctl.failed)
+      write_partition<PW>(p, M, b0, nb, ctl.excl, owner_mode, gkey, gpay, owner, gst, soff, att, Sp);
     if (t == 0) flush_stats(p, j, ctl);
     __syncthreads();
   }
@@ -891,7 +896,7 @@ __global__ void __launch_bounds__(kPartThreads, 1) k_part_overflow(PassDev p) {
   uint64_t* gpay = p.ovf_pay + PW * e0;
   for (uint32_t i = t; i < kB; i += kPartThreads) cnt[i] = 0;
   if (t == 0) {
-    ctl.maxs = ctl.maxatt = ctl.nonempty = ctl.nbig = 0;
+    ctl.maxs = ctl.maxatt = ctl.nonempty = ctl.nbig = ctl.failed = 0;
     ctl.attsum = 0;
   }
   __syncthreads();
@@ -915,7 +920,8 @@ __global__ void __launch_bounds__(kPartThreads, 1) k_part_overflow(PassDev p) {
   __syncthreads();
   search_partition<PW>(p, M, j, b0, nb, M.slot_base + excl, owner_mode, gkey, gpay, owner, gst, soff,
                        att, ctl);
-  write_partition<PW>(p, M, b0, nb, excl, owner_mode, gkey, gpay, owner, gst, soff, att, Sp);
+  if (!ctl.failed)
+    write_partition<PW>(p, M, b0, nb, excl, owner_mode, gkey, gpay, owner, gst, soff, att, Sp);
   if (t == 0) flush_stats(p, j, ctl);
 }
 

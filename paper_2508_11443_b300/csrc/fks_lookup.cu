@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(kLookupThreads) k_lookup_bytes(LookupMap M,
     const int64_t o1 = __ldg(reinterpret_cast<const long long*>(qoffs) + i + 1);
     int64_t v = absent;
     bool hit = false;
-    if (o1 >= o0 && o1 - o0 < (int64_t(1) << 24)) hit = lookup_one_bytes(M, qctx + o0, uint32_t(o1 - o0), &v);
+    if (o0 >= 0 && o1 >= o0 && o1 - o0 < (int64_t(1) << 24)) hit = lookup_one_bytes(M, qctx + o0, uint32_t(o1 - o0), &v);
     if (!hit) v = absent;
     if (out) {
       if (kI64) static_cast<int64_t*>(out)[i] = v;
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(kLookupThreads) k_lookup_batched(
         const uint32_t id = __ldg(ids + base + i);
         const int64_t o0 = __ldg(reinterpret_cast<const long long*>(qoffs) + base + i);
         const int64_t o1 = __ldg(reinterpret_cast<const long long*>(qoffs) + base + i + 1);
-        if (id < m && o1 >= o0 && o1 - o0 < (int64_t(1) << 24))
+        if (id < m && o0 >= 0 && o1 >= o0 && o1 - o0 < (int64_t(1) << 24))
           hit[i] = lookup_one_bytes(maps[id], qctx + o0, uint32_t(o1 - o0), &v[i]);
         if (!hit[i]) v[i] = absent;
       }
