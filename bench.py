@@ -72,13 +72,21 @@ def load_traffic():
     return out
 
 
-def kernel_digest() -> str:
+# source files each kernel is compiled from (digest ties ncu counters to code)
+KERNEL_SOURCES = {
+    "k_lookup_u64": ["fks_device.cuh", "fks_internal.cuh", "fks_lookup.cu"],
+    "k_part_build": ["fks_device.cuh", "fks_internal.cuh", "fks_build.cu"],
+    "k_partition_scatter": ["fks_device.cuh", "fks_internal.cuh", "fks_build.cu"],
+    "k_partition_count": ["fks_device.cuh", "fks_internal.cuh", "fks_build.cu"],
+}
+
+
+def kernel_digest(kernel: str) -> str:
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2508_11443_b300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in sorted(KERNEL_SOURCES[kernel]):
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:12]
 
 
@@ -324,9 +332,8 @@ def main():
         v["frac"] = v["GBps"] / hbm
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     traffic = load_traffic()
-    dig = kernel_digest()
     tr = None
-    if dom in traffic and traffic[dom][1] == dig:
+    if dom in traffic and traffic[dom][1] == kernel_digest(dom):
         tr = traffic[dom][0]
     D = kernels[dom]
     roofline = {"bound": "hbm", "achieved": D["GBps"], "peak": hbm, "unit": "GB/s",

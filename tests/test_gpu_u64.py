@@ -140,11 +140,20 @@ def test_duplicates_rejected(F):
 
 
 def test_forced_reseed_parity(F):
-    for seed in range(6):
-        keys = W.key_stream(40 + seed, 7)
-        om = O.build_u64(keys, np.arange(7), seed=seed, bound_factor=1, round_cap=400)
-        gm = gpu_build(F, keys, np.arange(7), seed, bound_factor=1, round_cap=400)
-        assert_same_tables(F, gm, om)
+    """bound 1 admits only all-singleton bucket layouts: many level-one rounds;
+    the device agrees with the oracle on the outcome and on the table."""
+    status_map = {O.BUILD_FAILED: F.FKS_ERR_BUILD_FAILED, O.DUPLICATE_KEY: F.FKS_ERR_DUPLICATE_KEY}
+    for n in (5, 7):
+        for seed in range(6):
+            keys = W.key_stream(40 + seed, n)
+            om = O.build_u64(keys, np.arange(n), seed=seed, bound_factor=1, round_cap=400)
+            if om.status == O.OK:
+                gm = gpu_build(F, keys, np.arange(n), seed, bound_factor=1, round_cap=400)
+                assert_same_tables(F, gm, om)
+            else:
+                with pytest.raises(F.FksError) as e:
+                    gpu_build(F, keys, np.arange(n), seed, bound_factor=1, round_cap=400)
+                assert e.value.status == status_map[om.status]
     keys = W.key_stream(4, 400)
     assert O.build_u64(keys, np.arange(400), seed=2, bound_factor=1, round_cap=3).status == O.BUILD_FAILED
     with pytest.raises(F.FksError) as e:
