@@ -184,6 +184,38 @@ fks_status fks_lookup_batched(fks_mapset_t set, const uint32_t* map_ids, const u
 uint32_t fks_mapset_size(fks_mapset_t set);
 fks_map_t fks_mapset_get(fks_mapset_t set, uint32_t j);
 
+/* ------------------------------------------------------------------ no allocation
+ * fks_build_u64_noalloc -- the same build as fks_build_u64, for callers that
+ * must not allocate device memory: a service whose device memory is all
+ * pre-reserved in its own pool or budget (a library allocation would bypass
+ * it, or fail), or a latency-critical path that cannot afford cudaMalloc /
+ * cudaFree, which may synchronise the device.  The paper has no counterpart;
+ * this is an engineering entry point of this library.
+ *
+ * Nothing is allocated: the caller passes the inputs and the output tables,
+ * and the build's scratch is one fixed device array compiled into the
+ * library (about 8.4 MB, held on every GPU that loads the library until the
+ * process exits).  Hence n <= FKS_NOALLOC_MAX_KEYS; larger n returns
+ * FKS_ERR_INVALID_ARG.
+ *   keys, vals, val_type, n, seed, opts   as for fks_build_u64
+ *   desc_out       uint64[n] (device): the bucket descriptors
+ *   slots_out      slot_capacity slots of 16 bytes (device), slot_capacity >=
+ *                  bound_factor * n; the first info.slots slots are the table
+ *   h_info         (host, nullable) sizes and statistics of the result
+ * The tables written are byte-for-byte those fks_build_u64 would build for
+ * the same (keys, values, seed), as fks_map_export returns them.
+ * The first call on a device looks up the scratch array's device address
+ * (once per device); make that first call before any stream capture.
+ * All calls share the scratch array: calls whose work overlaps on the GPU
+ * (two host threads, or two streams) race and must be serialised by the
+ * caller.  Blocks until the result is known, like fks_build_u64.  Returns a
+ * status only (fks_last_error is not updated). */
+#define FKS_NOALLOC_MAX_KEYS 262144u
+fks_status fks_build_u64_noalloc(const uint64_t* keys, const void* vals, fks_val_type val_type,
+                                 uint64_t n, uint64_t seed, const fks_build_opts* opts,
+                                 uint64_t* desc_out, void* slots_out, uint64_t slot_capacity,
+                                 fks_map_info_t* h_info, fks_stream_t stream);
+
 /* ------------------------------------------------------------------ tables
  * fks_map_info -- sizes and build statistics (host struct). */
 fks_status fks_map_info(fks_map_t map, fks_map_info_t* h_out);

@@ -226,6 +226,25 @@ def fks_lookup_batched(s: MapSet, map_ids, q=None, qctx=None, qoffs=None, out_va
                                     _ptr(out_vals), _ptr(out_found), absent, _stream(stream)))
 
 
+def fks_build_u64_noalloc(keys, vals, seed: int, desc_out, slots_out,
+                          opts: fks_build_opts | None = None, stream=None) -> fks_map_info_t:
+    """The allocation-free build: the caller owns every output buffer
+    (desc_out int64[n], slots_out int64[2 * capacity]); scratch comes from a
+    fixed array inside the library (n <= 262144)."""
+    f = lib().fks_build_u64_noalloc
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
+                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64,
+                  ctypes.POINTER(fks_map_info_t), ctypes.c_void_p]
+    f.restype = ctypes.c_int
+    info = fks_map_info_t()
+    st = f(_ptr(keys), _ptr(vals), _val_type(vals), keys.numel(), seed & (2**64 - 1),
+           ctypes.byref(opts) if opts else None, _ptr(desc_out), _ptr(slots_out),
+           slots_out.numel() // 2, ctypes.byref(info), _stream(stream))
+    if st != FKS_OK:
+        raise FksError(st, fks_status_str(st))
+    return info
+
+
 def fks_map_info(m: Map) -> fks_map_info_t:
     info = fks_map_info_t()
     _check(lib().fks_map_info(m.handle, ctypes.byref(info)))
