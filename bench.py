@@ -236,7 +236,8 @@ def main():
             build_ms.append(e0.elapsed_time(e1))
             lookup_ms.append(e1.elapsed_time(e2))
             step_ms.append(e0.elapsed_time(e2))
-            part_ms.append((prof.count_ms, prof.scan_ms, prof.scatter_ms, prof.part_build_ms))
+            part_ms.append((prof.count_ms, prof.scan_ms, prof.scatter_ms, prof.part_build_ms,
+                            prof.group_ms, prof.grouping_levels))
             nonempty.append(info.nonempty_buckets / info.n)
             S.append(info.slots / info.n)
         del m
@@ -322,15 +323,22 @@ def main():
                          "model": f"{lookup_bytes_per_query(HIT, ne):.2f} B/query x {nq}"},
         "k_part_build": {"ms": pb, "bytes": part_build_bytes_per_key(s_n) * n,
                          "model": f"{part_build_bytes_per_key(s_n):.2f} B/key x {n}"},
-        "k_partition_scatter": {"ms": med([p[2] for p in part_ms]), "bytes": 32.0 * n,
-                                "model": f"32 B/key x {n}"},
-        "k_partition_count": {"ms": med([p[0] for p in part_ms]), "bytes": 8.0 * n,
-                              "model": f"8 B/key x {n}"},
     }
+    two_level = part_ms[-1][5] == 2
+    if two_level:
+        # count A 8 + scatter A 16 read + 20 write + count B 4 + scatter B 20 read + 16 write
+        kernels["grouping_2level"] = {"ms": med([p[4] for p in part_ms]), "bytes": 84.0 * n,
+                                      "model": f"84 B/key x {n} (12 kernels)"}
+    else:
+        kernels["k_partition_scatter"] = {"ms": med([p[2] for p in part_ms]), "bytes": 32.0 * n,
+                                          "model": f"32 B/key x {n}"}
+        kernels["k_partition_count"] = {"ms": med([p[0] for p in part_ms]), "bytes": 8.0 * n,
+                                        "model": f"8 B/key x {n}"}
     for k, v in kernels.items():
         v["GBps"] = v["bytes"] / (v["ms"] / 1e3) / 1e9
         v["frac"] = v["GBps"] / hbm
-    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    # the dominant single kernel carries the roofline object
+    dom = max(("k_lookup_u64", "k_part_build"), key=lambda k: kernels[k]["ms"])
     traffic = load_traffic()
     tr = None
     if dom in traffic and traffic[dom][1] == kernel_digest(dom):
@@ -351,8 +359,9 @@ def main():
         "build_keys_per_s": n * world / (med(build_ms) / 1e3),
         "lookups_per_s": nq * world / (lk / 1e3),
         "build_ms": med(build_ms), "lookup_ms": lk,
-        "phases_ms": {"count": med([p[0] for p in part_ms]), "scan": med([p[1] for p in part_ms]),
-                      "scatter": med([p[2] for p in part_ms]), "part_build": pb},
+        "phases_ms": ({"grouping": med([p[4] for p in part_ms]), "part_build": pb} if two_level else
+                      {"count": med([p[0] for p in part_ms]), "scan": med([p[1] for p in part_ms]),
+                       "scatter": med([p[2] for p in part_ms]), "part_build": pb}),
         "S_over_n": s_n, "nonempty_frac": ne,
         "roofline": roofline,
         "kernels": {k: {"ms": round(v["ms"], 4), "GBps": round(v["GBps"], 1),

@@ -98,14 +98,18 @@ typedef struct {
 
 /* Phase timings of the last build on the calling thread (CUDA events on the
  * build's stream; summed over level-one passes).  Recorded only while
- * fks_profile_enable(1) is in effect on that thread. */
+ * fks_profile_enable(1) is in effect on that thread.  Keys are grouped by
+ * level-one partition either in one level (count, scan, scatter) or, for
+ * large builds, in two radix levels, reported together in group_ms. */
 typedef struct {
   float fingerprint_ms; /* string maps: fingerprints of the keys            */
-  float count_ms;       /* level-one hash + keys per partition              */
-  float scan_ms;        /* scan of the partition counts                     */
-  float scatter_ms;     /* keys scattered into partition ranges             */
+  float count_ms;       /* one level: level-one hash + keys per partition   */
+  float scan_ms;        /* one level: scan of the partition counts          */
+  float scatter_ms;     /* one level: keys scattered into partition ranges  */
   float part_build_ms;  /* per-partition Hist, Presum, make_2, placement    */
   uint32_t passes;      /* level-one passes run                             */
+  uint32_t grouping_levels; /* 1 or 2                                       */
+  float group_ms;       /* two levels: the whole grouping                   */
 } fks_build_profile;
 
 /* ------------------------------------------------------------------ build

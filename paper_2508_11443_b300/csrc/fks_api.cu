@@ -66,9 +66,13 @@ struct ProfileEvents {
   void accumulate(fks_build_profile* p, bool strings) const {
     if (!ok) return;
     float ms = 0;
-    if (cudaEventElapsedTime(&ms, pe.ev[0], pe.ev[1]) == cudaSuccess) p->count_ms += ms;
-    if (cudaEventElapsedTime(&ms, pe.ev[1], pe.ev[2]) == cudaSuccess) p->scan_ms += ms;
-    if (cudaEventElapsedTime(&ms, pe.ev[2], pe.ev[3]) == cudaSuccess) p->scatter_ms += ms;
+    if (p->grouping_levels == 2) {
+      if (cudaEventElapsedTime(&ms, pe.ev[0], pe.ev[3]) == cudaSuccess) p->group_ms += ms;
+    } else {
+      if (cudaEventElapsedTime(&ms, pe.ev[0], pe.ev[1]) == cudaSuccess) p->count_ms += ms;
+      if (cudaEventElapsedTime(&ms, pe.ev[1], pe.ev[2]) == cudaSuccess) p->scan_ms += ms;
+      if (cudaEventElapsedTime(&ms, pe.ev[2], pe.ev[3]) == cudaSuccess) p->scatter_ms += ms;
+    }
     if (cudaEventElapsedTime(&ms, pe.ev[3], pe.ev[4]) == cudaSuccess) p->part_build_ms += ms;
     if (strings && cudaEventElapsedTime(&ms, fp0, fp1) == cudaSuccess) p->fingerprint_ms += ms;
     p->passes += 1;
@@ -229,6 +233,9 @@ static thread_local int g_hold_first_partition = 0;
 extern "C" void fks_test_hold_first_partition(int on) { g_hold_first_partition = on; }
 
 // ---------------------------------------------------------------- the build
+// Passes with at least this many keys group them in two radix levels.
+constexpr uint64_t kSplitMinKeys = 1ull << 20;
+
 struct BuildIn {
   fks_key_kind kind;
   const uint64_t* keys;  // u64 keys (input numbering)
@@ -308,6 +315,21 @@ static fks_status build_impl(const BuildIn& in, const Opts& o, const Alloc& A, c
   const size_t s_qseg = cs.take<uint32_t>(m + 1);
   const size_t s_stat = cs.take<MapStatus>(m);
   const size_t s_fps = cs.take<uint64_t>(str ? total + 1 : 0);
+  // two-level grouping for large builds
+  const SplitShape shape = split_shape(uint32_t(P_all), total);
+  const bool use_split = total >= kSplitMinKeys && shape.ok;
+  size_t s_ka = 0, s_pa = 0, s_ga = 0, s_hist = 0, s_sums = 0, s_sa = 0, s_tb = 0;
+  size_t hist_words = 0;
+  if (use_split) {
+    hist_words = split_hist_words(shape);
+    s_ka = cs.take<uint64_t>(total);
+    s_pa = cs.take<uint64_t>(total * PW);
+    s_ga = cs.take<uint32_t>(total);
+    s_hist = cs.take<uint32_t>(hist_words);
+    s_sums = cs.take<uint32_t>(split_sum_words(shape));
+    s_sa = cs.take<uint64_t>(shape.binsA + 1);
+    s_tb = cs.take<uint32_t>(shape.binsA + 1);
+  }
   uint8_t* scr = static_cast<uint8_t*>(A.get(cs.off, st));
   if (!scr) {
     A.put(block, cm.off, st);
@@ -415,7 +437,29 @@ static fks_status build_impl(const BuildIn& in, const Opts& o, const Alloc& A, c
     if (prof.ok && str) cudaEventRecord(prof.fp0, st);
     if (str) FKS_PASS(launch_fingerprints(in.ctx, in.offs, total, d_maps, d_pseg, ma, pe, fps, d_stat, st));
     if (prof.ok && str) cudaEventRecord(prof.fp1, st);
-    FKS_PASS(launch_pass(p, str, sms, st, prof.ok ? &prof.pe : nullptr));
+    SplitShape sh = split_shape(pp, pe);
+    const bool split_pass = use_split && sh.ok && split_hist_words(sh) <= hist_words &&
+                            sh.binsA <= shape.binsA && pe >= kSplitMinKeys;
+    if (split_pass) {
+      SplitDev sd{};
+      sd.binsA = sh.binsA;
+      sd.binsB = sh.binsB;
+      sd.shiftB = sh.shiftB;
+      sd.tilesA = sh.tilesA;
+      sd.tilesB_max = sh.tilesB_max;
+      sd.histA = sd.histB = reinterpret_cast<uint32_t*>(scr + s_hist);
+      sd.sums = reinterpret_cast<uint32_t*>(scr + s_sums);
+      sd.startA = reinterpret_cast<uint64_t*>(scr + s_sa);
+      sd.tstartB = reinterpret_cast<uint32_t*>(scr + s_tb);
+      sd.keyA = reinterpret_cast<uint64_t*>(scr + s_ka);
+      sd.payA = reinterpret_cast<uint64_t*>(scr + s_pa);
+      sd.gpA = reinterpret_cast<uint32_t*>(scr + s_ga);
+      profile.grouping_levels = 2;
+      FKS_PASS(launch_pass_split(p, sd, str, sms, st, prof.ok ? &prof.pe : nullptr));
+    } else {
+      profile.grouping_levels = 1;
+      FKS_PASS(launch_pass(p, str, sms, st, prof.ok ? &prof.pe : nullptr));
+    }
     // ---- status
     const size_t down_bytes = sizeof(MapStatus) * ma + 16;
     uint8_t* down = static_cast<uint8_t*>(g_pin_down.get(down_bytes));

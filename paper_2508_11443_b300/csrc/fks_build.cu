@@ -274,12 +274,14 @@ struct Smem {
   static constexpr uint32_t kGst = kCnt + kB * 4;
   static constexpr uint32_t kSoff = kGst + (kB + 4) * 4;
   static constexpr uint32_t kAtt = kSoff + kB * 4;
-  static constexpr uint32_t kBytes = align16(kAtt + kB * 2);
+  static constexpr uint32_t kWork = align16(kAtt + kB * 2);  // buckets that need a search
+  static constexpr uint32_t kBytes = align16(kWork + kB * 2);
 };
 
 struct PartCtl {
   uint32_t gp, skip, nbig, maxs, maxatt, flag_a, flag_b, nonempty;
   uint32_t failed;  // a bucket found no constants: this pass of the map is discarded
+  uint32_t nwork;   // entries of the search worklist
   uint32_t next_gp, next_issued, abort;
   uint64_t excl, Spart, attsum;
   unsigned long long fillmin;  // (slot << 32) | member of a CTA-searched bucket
@@ -492,7 +494,8 @@ enum { kSearchDup = -1, kSearchNext = -2 };
 // into s^2 slots are pairwise distinct.
 template <int PW>
 __device__ int search_thread(const PassDev& p, const uint64_t* k, const uint64_t* gpay,
-                             uint32_t g0, uint32_t s, uint64_t seed, uint32_t round, uint32_t b) {
+                             uint32_t g0, uint32_t s, uint64_t seed, uint32_t round, uint32_t b,
+                             HashConsts* found) {
   const uint32_t m = s * s;
   for (uint32_t a = 0; a < p.cfg.attempt_cap; ++a) {
     if (a == kDupCheckAttempt) {
@@ -523,7 +526,10 @@ __device__ int search_thread(const PassDev& p, const uint64_t* k, const uint64_t
       }
     }
     if (a < p.cfg.reject) continue;
-    if (!col) return int(a);
+    if (!col) {
+      *found = c;
+      return int(a);
+    }
   }
   return kSearchNext;
 }
@@ -654,32 +660,39 @@ __device__ void search_partition(const PassDev& p, const MapRegs& M, uint32_t j,
                                  uint32_t nb, uint64_t slot_part, bool owner_mode,
                                  const uint64_t* gkey, const uint64_t* gpay, uint16_t* owner,
                                  const uint32_t* gst, const uint32_t* soff, uint16_t* att,
-                                 PartCtl& ctl) {
-  uint32_t my_max = 0;
-  uint64_t my_sum = 0;
+                                 uint16_t* work, PartCtl& ctl) {
+  // empty and single-key buckets need no search (attempt 0); the others are
+  // compacted into a worklist so that searching lanes sit side by side
   for (uint32_t lb = threadIdx.x; lb < nb; lb += kPartThreads) {
     const uint32_t g0 = gst[lb], s = gst[lb + 1] - g0;
-    uint16_t a_out = 0;
+    att[lb] = 0;
     if (s == 1) {
       if (owner_mode) owner[soff[lb]] = uint16_t(g0);
       else write_slot<PW>(p, slot_part + soff[lb], gkey[g0], gpay + PW * g0, false);
     } else if (s > 1 && s <= kThreadSearchMax) {
-      const int a = search_thread<PW>(p, gkey + g0, gpay, g0, s, M.seed, M.round, b0 + lb);
-      if (a >= 0) {
-        a_out = uint16_t(a);
-        my_max = max(my_max, uint32_t(a));
-        my_sum += uint64_t(a);
-        const HashConsts c = derive(M.seed, M.round, b0 + lb, uint32_t(a));
-        place_thread<PW>(p, gkey + g0, gpay, g0, s, c, owner, soff[lb], slot_part + soff[lb],
-                         owner_mode);
-      } else {
-        atomicExch(a == kSearchDup ? &p.status[j].dup : &p.status[j].next_round, 1u);
-        ctl.failed = 1;
-      }
+      work[atomicAdd(&ctl.nwork, 1u)] = uint16_t(lb);
     } else if (s > kThreadSearchMax) {
       atomicAdd(&ctl.nbig, 1u);
     }
-    att[lb] = a_out;
+  }
+  __syncthreads();
+  uint32_t my_max = 0;
+  uint64_t my_sum = 0;
+  const uint32_t nwork = ctl.nwork;
+  for (uint32_t w = threadIdx.x; w < nwork; w += kPartThreads) {
+    const uint32_t lb = work[w];
+    const uint32_t g0 = gst[lb], s = gst[lb + 1] - g0;
+    HashConsts c;
+    const int a = search_thread<PW>(p, gkey + g0, gpay, g0, s, M.seed, M.round, b0 + lb, &c);
+    if (a >= 0) {
+      att[lb] = uint16_t(a);
+      my_max = max(my_max, uint32_t(a));
+      my_sum += uint64_t(a);
+      place_thread<PW>(p, gkey + g0, gpay, g0, s, c, owner, soff[lb], slot_part + soff[lb], owner_mode);
+    } else {
+      atomicExch(a == kSearchDup ? &p.status[j].dup : &p.status[j].next_round, 1u);
+      ctl.failed = 1;
+    }
   }
   if (my_max) atomicMax(&ctl.maxatt, my_max);
   if (my_sum) atomicAdd(reinterpret_cast<unsigned long long*>(&ctl.attsum), my_sum);
@@ -691,8 +704,8 @@ __device__ void search_partition(const PassDev& p, const MapRegs& M, uint32_t j,
       search_place_cta<PW>(p, gkey + g0, gpay, g0, s, M.seed, M.round, b0 + lb, owner, soff[lb],
                            slot_part + soff[lb], owner_mode, j, ctl, att + lb);
     }
+    __syncthreads();
   }
-  __syncthreads();
 }
 
 // Descriptors of the partition's buckets and, in owner mode, its slot image
@@ -740,6 +753,7 @@ __global__ void __launch_bounds__(kPartThreads, PW == 1 ? 2 : 1) k_part_build(Pa
   uint32_t* gst = reinterpret_cast<uint32_t*>(smem + L::kGst);
   uint32_t* soff = reinterpret_cast<uint32_t*>(smem + L::kSoff);
   uint16_t* att = reinterpret_cast<uint16_t*>(smem + L::kAtt);
+  uint16_t* work = reinterpret_cast<uint16_t*>(smem + L::kWork);
   __shared__ PartCtl ctl;
   __shared__ __align__(8) uint64_t bar;
   const uint32_t t = threadIdx.x;
@@ -763,10 +777,6 @@ __global__ void __launch_bounds__(kPartThreads, PW == 1 ? 2 : 1) k_part_build(Pa
     const uint64_t e0 = p.part_start[gp], e1 = p.part_start[gp + 1];
     const uint32_t ne = uint32_t(e1 - e0 < 0xFFFFFFFFull ? e1 - e0 : 0xFFFFFFFFull);
     for (uint32_t i = t; i < kB; i += kPartThreads) cnt[i] = 0;
-    if (t == 0) {
-      ctl.maxs = ctl.maxatt = ctl.nonempty = ctl.nbig = ctl.failed = 0;
-      ctl.attsum = 0;
-    }
     if (issued) {  // bounded wait for the staged copy
       uint32_t polls = 0;
       while (!mbar_try_wait(&bar, parity)) {
@@ -781,6 +791,10 @@ __global__ void __launch_bounds__(kPartThreads, PW == 1 ? 2 : 1) k_part_build(Pa
     if (ctl.abort) {
       if (t == 0) atomicExch(&p.status[j].timeout, 1u);
       break;
+    }
+    if (t == 0) {  // every reader of last iteration's values passed the barrier above
+      ctl.maxs = ctl.maxatt = ctl.nonempty = ctl.nbig = ctl.failed = ctl.nwork = 0;
+      ctl.attsum = 0;
     }
     const bool overflow = ne > kCap;
     const uint32_t shift = uint32_t(e0 & 1ull);  // raw key index of element e0
@@ -857,11 +871,10 @@ __global__ void __launch_bounds__(kPartThreads, PW == 1 ? 2 : 1) k_part_build(Pa
       continue;
     }
     search_partition<PW>(p, M, j, b0, nb, M.slot_base + ctl.excl, owner_mode, gkey, gpay, owner, gst,
-                         soff, att, ctl);
+                         soff, att, work, ctl);
     if (!ctl.failed)
       write_partition<PW>(p, M, b0, nb, ctl.excl, owner_mode, gkey, gpay, owner, gst, soff, att, Sp);
     if (t == 0) flush_stats(p, j, ctl);
-    __syncthreads();
   }
   // never leave with a bulk copy in flight
   if (t == 0 && ctl.next_issued && ctl.abort) {
@@ -883,6 +896,7 @@ __global__ void __launch_bounds__(kPartThreads, 1) k_part_overflow(PassDev p) {
   uint32_t* gst = reinterpret_cast<uint32_t*>(smem + L::kGst);
   uint32_t* soff = reinterpret_cast<uint32_t*>(smem + L::kSoff);
   uint16_t* att = reinterpret_cast<uint16_t*>(smem + L::kAtt);
+  uint16_t* work = reinterpret_cast<uint16_t*>(smem + L::kWork);
   __shared__ PartCtl ctl;
   const uint32_t t = threadIdx.x;
   const uint32_t gp = p.ovf_list[blockIdx.x];
@@ -896,7 +910,7 @@ __global__ void __launch_bounds__(kPartThreads, 1) k_part_overflow(PassDev p) {
   uint64_t* gpay = p.ovf_pay + PW * e0;
   for (uint32_t i = t; i < kB; i += kPartThreads) cnt[i] = 0;
   if (t == 0) {
-    ctl.maxs = ctl.maxatt = ctl.nonempty = ctl.nbig = ctl.failed = 0;
+    ctl.maxs = ctl.maxatt = ctl.nonempty = ctl.nbig = ctl.failed = ctl.nwork = 0;
     ctl.attsum = 0;
   }
   __syncthreads();
@@ -919,7 +933,7 @@ __global__ void __launch_bounds__(kPartThreads, 1) k_part_overflow(PassDev p) {
   }
   __syncthreads();
   search_partition<PW>(p, M, j, b0, nb, M.slot_base + excl, owner_mode, gkey, gpay, owner, gst, soff,
-                       att, ctl);
+                       att, work, ctl);
   if (!ctl.failed)
     write_partition<PW>(p, M, b0, nb, excl, owner_mode, gkey, gpay, owner, gst, soff, att, Sp);
   if (t == 0) flush_stats(p, j, ctl);
@@ -1039,6 +1053,24 @@ cudaError_t launch_pass(const PassDev& p, bool strings, int sms, cudaStream_t st
   if (e != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev->ev[4], stream);
   note_launches(4);
+  return cudaSuccess;
+}
+
+cudaError_t launch_pass_split(const PassDev& p, const SplitDev& s, bool strings, int sms,
+                              cudaStream_t stream, const PassEvents* ev) {
+  if (p.total == 0 || p.P == 0) return cudaSuccess;
+  if (ev) cudaEventRecord(ev->ev[0], stream);
+  cudaError_t e = launch_split(p, s, strings, stream);
+  if (e != cudaSuccess) return e;
+  if (ev) {
+    cudaEventRecord(ev->ev[1], stream);
+    cudaEventRecord(ev->ev[2], stream);
+    cudaEventRecord(ev->ev[3], stream);
+  }
+  e = strings ? launch_build_kernel<2>(p, sms, stream) : launch_build_kernel<1>(p, sms, stream);
+  if (e != cudaSuccess) return e;
+  if (ev) cudaEventRecord(ev->ev[4], stream);
+  note_launches(1);
   return cudaSuccess;
 }
 

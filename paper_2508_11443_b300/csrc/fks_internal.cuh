@@ -104,6 +104,27 @@ struct PassEvents {
   cudaEvent_t ev[5];
 };
 
+// Two-level grouping of large passes (fks_split.cu).
+struct SplitShape {
+  uint32_t binsA, binsB, shiftB, tilesA, tilesB_max;
+  bool ok;
+};
+struct SplitDev {
+  uint32_t binsA, binsB, shiftB, tilesA, tilesB_max;
+  uint32_t* histA;    // [binsA * tilesA] (may alias histB)
+  uint32_t* histB;    // [binsB * tilesB_max]
+  uint32_t* sums;     // block sums of the device-wide scan
+  uint64_t* startA;   // [binsA + 1] level-A bin starts
+  uint32_t* tstartB;  // [binsA + 1] first level-B tile of each level-A bin
+  uint64_t* keyA;     // level-A output: keys, payloads, partition of each key
+  uint64_t* payA;
+  uint32_t* gpA;
+};
+SplitShape split_shape(uint32_t P, uint64_t total);
+size_t split_hist_words(const SplitShape& sh);
+size_t split_sum_words(const SplitShape& sh);
+cudaError_t launch_split(const PassDev& p, const SplitDev& s, bool strings, cudaStream_t stream);
+
 // Launchers (fks_build.cu).
 cudaError_t launch_fingerprints(const uint8_t* ctx, const int64_t* offs, uint64_t n,
                                 const MapDev* maps, const uint64_t* pass_seg, uint32_t m,
@@ -111,6 +132,10 @@ cudaError_t launch_fingerprints(const uint8_t* ctx, const int64_t* offs, uint64_
                                 cudaStream_t stream);
 cudaError_t launch_pass(const PassDev& p, bool strings, int sms, cudaStream_t stream,
                         const PassEvents* events);
+// The same pass with the keys grouped by launch_split instead of the
+// single-level partition scatter.
+cudaError_t launch_pass_split(const PassDev& p, const SplitDev& s, bool strings, int sms,
+                              cudaStream_t stream, const PassEvents* events);
 cudaError_t launch_overflow(const PassDev& p, bool strings, uint32_t count, cudaStream_t stream);
 cudaError_t launch_dupcheck(const uint64_t* hkeys, const int64_t* offs, const uint8_t* ctx,
                             uint64_t n, uint64_t* table, uint32_t* table_idx, uint64_t table_size,

@@ -20,16 +20,28 @@ namespace {
 
 constexpr int kLookupThreads = 256;
 
-__device__ __forceinline__ uint64_t ld_na_u64(const uint64_t* p) {
+// L2 policies: descriptors are kept (evict_last) so the L2 holds as many of
+// them as fits; slots are read once (evict_first).
+__device__ __forceinline__ uint64_t policy_keep() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ uint64_t policy_stream() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ uint64_t ld_na_u64(const uint64_t* p, uint64_t pol) {
   uint64_t v;
-  asm volatile("ld.global.nc.L1::no_allocate.u64 %0, [%1];" : "=l"(v) : "l"(p));
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.u64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol));
   return v;
 }
-__device__ __forceinline__ ulonglong2 ld_na_u128(const uint64_t* p) {
+__device__ __forceinline__ ulonglong2 ld_na_u128(const uint64_t* p, uint64_t pol) {
   ulonglong2 v;
-  asm volatile("ld.global.nc.L1::no_allocate.v2.u64 {%0, %1}, [%2];"
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.u64 {%0, %1}, [%2], %3;"
                : "=l"(v.x), "=l"(v.y)
-               : "l"(p));
+               : "l"(p), "l"(pol));
   return v;
 }
 
@@ -55,6 +67,7 @@ __global__ void __launch_bounds__(kLookupThreads) k_lookup_u64(LookupMap M,
                                                                uint8_t* __restrict__ found,
                                                                int64_t absent, int vec) {
   const uint64_t stride = uint64_t(gridDim.x) * blockDim.x * kQ;
+  const uint64_t keep = policy_keep(), strm = policy_stream();
   for (uint64_t base = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) * kQ; base < nq;
        base += stride) {
     const bool full = vec && base + kQ <= nq;
@@ -75,7 +88,7 @@ __global__ void __launch_bounds__(kLookupThreads) k_lookup_u64(LookupMap M,
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
       b[i] = reduce32(hash32(M.c1, k[i]), M.n);
-      d[i] = ld_na_u64(M.desc + b[i]);
+      d[i] = ld_na_u64(M.desc + b[i], keep);
     }
     ulonglong2 sl[kQ];
 #pragma unroll
@@ -85,7 +98,7 @@ __global__ void __launch_bounds__(kLookupThreads) k_lookup_u64(LookupMap M,
       if (s) {
         const HashConsts c = derive(M.seed, M.round, b[i], desc_attempt(d[i]));
         const uint32_t jj = desc_off(d[i]) + reduce32(hash32(c, k[i]), s * s);
-        sl[i] = ld_na_u128(M.slots + 2ull * jj);
+        sl[i] = ld_na_u128(M.slots + 2ull * jj, strm);
       }
     }
     int64_t v[kQ];
@@ -133,21 +146,22 @@ __global__ void __launch_bounds__(kLookupThreads) k_lookup_u64(LookupMap M,
 // One needle of a string map; returns whether it is present.
 __device__ __forceinline__ bool lookup_one_bytes(const LookupMap& M, const uint8_t* s,
                                                  uint32_t len, int64_t* val) {
+  const uint64_t keep = policy_keep(), strm = policy_stream();
   uint64_t h = len;
   const uint32_t words = (len + 3u) >> 2;
   for (uint32_t t = 0; t < words; ++t) h = addmod61(mulmod61(h, M.fpb), str_word(s, len, t));
   const uint32_t b = reduce32(hash32(M.c1, h), M.n);
-  const uint64_t d = ld_na_u64(M.desc + b);
+  const uint64_t d = ld_na_u64(M.desc + b, keep);
   const uint32_t sz = desc_s(d);
   if (!sz) return false;
   const HashConsts c = derive(M.seed, M.round, b, desc_attempt(d));
   const uint32_t jj = desc_off(d) + reduce32(hash32(c, h), sz * sz);
-  const ulonglong2 w0 = ld_na_u128(M.slots + 4ull * jj);
+  const ulonglong2 w0 = ld_na_u128(M.slots + 4ull * jj, strm);
   if (w0.x != h || offlen_len(w0.y) != len) return false;
   const uint8_t* ms = M.ctx + offlen_off(w0.y);
   for (uint32_t t = 0; t < words; ++t)
     if (str_word(ms, len, t) != str_word(s, len, t)) return false;
-  *val = int64_t(ld_na_u64(M.slots + 4ull * jj + 2));
+  *val = int64_t(ld_na_u64(M.slots + 4ull * jj + 2, strm));
   return true;
 }
 
@@ -184,6 +198,7 @@ __global__ void __launch_bounds__(kLookupThreads) k_lookup_batched(
     uint8_t* __restrict__ found, int64_t absent) {
   constexpr int kQ = 2;
   const uint64_t stride = uint64_t(gridDim.x) * blockDim.x * kQ;
+  const uint64_t keep = policy_keep(), strm = policy_stream();
   for (uint64_t base = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) * kQ; base < nq;
        base += stride) {
     int64_t v[kQ];
@@ -200,7 +215,7 @@ __global__ void __launch_bounds__(kLookupThreads) k_lookup_batched(
         b[i] = 0;
         if (id[i] < m) {
           b[i] = reduce32(hash32(maps[id[i]].c1, k[i]), maps[id[i]].n);
-          d[i] = ld_na_u64(maps[id[i]].desc + b[i]);
+          d[i] = ld_na_u64(maps[id[i]].desc + b[i], keep);
         }
       }
 #pragma unroll
@@ -212,7 +227,7 @@ __global__ void __launch_bounds__(kLookupThreads) k_lookup_batched(
           const LookupMap& M = maps[id[i]];
           const HashConsts c = derive(M.seed, M.round, b[i], desc_attempt(d[i]));
           const uint32_t jj = desc_off(d[i]) + reduce32(hash32(c, k[i]), s * s);
-          const ulonglong2 sl = ld_na_u128(M.slots + 2ull * jj);
+          const ulonglong2 sl = ld_na_u128(M.slots + 2ull * jj, strm);
           hit[i] = sl.x == k[i];
           if (hit[i]) v[i] = int64_t(sl.y);
         }

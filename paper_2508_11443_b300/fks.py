@@ -54,7 +54,8 @@ class fks_map_info_t(ctypes.Structure):
 class fks_build_profile(ctypes.Structure):
     _fields_ = [("fingerprint_ms", ctypes.c_float), ("count_ms", ctypes.c_float),
                 ("scan_ms", ctypes.c_float), ("scatter_ms", ctypes.c_float),
-                ("part_build_ms", ctypes.c_float), ("passes", ctypes.c_uint32)]
+                ("part_build_ms", ctypes.c_float), ("passes", ctypes.c_uint32),
+                ("grouping_levels", ctypes.c_uint32), ("group_ms", ctypes.c_float)]
 
 
 _lib = None

@@ -58,7 +58,8 @@ def assert_same_tables(F, gm, om):
     assert np.array_equal(slots, om.slots)
 
 
-@pytest.mark.parametrize("n", [1, 2, 3, 17, 1023, 1024, 1025, 5000, (1 << 16) + 7, 300001])
+@pytest.mark.parametrize("n", [1, 2, 3, 17, 1023, 1024, 1025, 5000, (1 << 16) + 7, 300001,
+                               (1 << 20) + 12345])
 def test_tables_and_lookups_bit_exact(F, n):
     w = W.u64_workload(n, 2 * n + 3, 0.5, seed=n)
     om = O.build_u64(w.keys, w.vals, seed=1234 + n)
@@ -181,7 +182,7 @@ def crafted_crowded_keys(seed, n_total, crowd):
     (more than one partition's shared-memory capacity)."""
     c1 = [np.uint64(x) for x in O.derive(seed, 0, O.TAG_L1, 0)]
     base = W.key_stream(77, n_total)
-    cand = W.key_stream(78, 400 * crowd)
+    cand = W.key_stream(78, int(crowd * n_total / 1024 * 1.3) + 1000)
     with np.errstate(over="ignore"):
         h = (c1[0] * (cand & np.uint64(0xFFFFFFFF)) + c1[1] * (cand >> np.uint64(32)) + c1[2]) >> np.uint64(32)
         b = (h * np.uint64(n_total)) >> np.uint64(32)
@@ -204,6 +205,17 @@ def test_overflow_partition_parity(F):
     out, found = gpu_lookup(F, gm, q)
     oo, of = O.lookup_u64(om, q)
     assert np.array_equal(out, oo) and np.array_equal(found, of)
+
+
+def test_overflow_partition_two_level_grouping(F):
+    """An oversized partition in a build large enough for the two-level grouping."""
+    n, seed = (1 << 20) + 100, 33
+    keys = crafted_crowded_keys(seed, n, 2600)
+    om = O.build_u64(keys, np.arange(n), seed=seed)
+    assert om.status == O.OK and om.round == 0
+    gm = gpu_build(F, keys, np.arange(n), seed)
+    assert F.fks_map_info(gm).overflow_partitions >= 1
+    assert_same_tables(F, gm, om)
 
 
 def test_deterministic_tables(F):
