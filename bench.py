@@ -17,7 +17,6 @@ import json
 import os
 import re
 import statistics
-import subprocess
 import sys
 import threading
 import time
@@ -91,51 +90,70 @@ def kernel_digest(kernel: str) -> str:
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons while running."""
+    """SM clock and clock-event (throttle) reasons sampled through NVML every
+    few milliseconds from a background thread (read-only queries).  mark()
+    brackets the timed region; summary() keeps the samples inside it."""
 
-    def __init__(self, index: int):
-        self.index = index
-        self.samples = []
-        self.proc = None
+    REASONS = (("hw_slowdown", "nvmlClocksEventReasonHwSlowdown"),
+               ("hw_thermal_slowdown", "nvmlClocksEventReasonHwThermalSlowdown"),
+               ("sw_thermal_slowdown", "nvmlClocksEventReasonSwThermalSlowdown"),
+               ("sw_power_cap", "nvmlClocksEventReasonSwPowerCap"),
+               ("hw_power_brake", "nvmlClocksEventReasonHwPowerBrakeSlowdown"))
+
+    def __init__(self, index: int, period_s: float = 0.002):
+        self.index, self.period = index, period_s
+        self.samples = []  # (t, sm_mhz, reasons bitmask)
+        self.window = None
+        self.max_mhz = None
+        self.err = None
 
     def __enter__(self):
-        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
-             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-             "clocks_event_reasons.sw_power_cap")
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.thread = threading.Thread(target=self._read, daemon=True)
+            import pynvml
+            pynvml.nvmlInit()
+            self.nv = pynvml
+            self.h = pynvml.nvmlDeviceGetHandleByIndex(self.index)
+            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM)
+            self.stop = threading.Event()
+            self.thread = threading.Thread(target=self._run, daemon=True)
             self.thread.start()
-        except Exception:
-            self.proc = None
+        except Exception as e:  # no NVML: report it, keep running
+            self.err = repr(e)
         return self
 
-    def _read(self):
-        for line in self.proc.stdout:
-            parts = [p.strip() for p in line.split(",")]
-            if len(parts) == 7:
-                self.samples.append(parts)
+    def _run(self):
+        nv, h = self.nv, self.h
+        while not self.stop.is_set():
+            try:
+                self.samples.append((time.perf_counter(), nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM),
+                                     nv.nvmlDeviceGetCurrentClocksEventReasons(h)))
+            except Exception as e:
+                self.err = repr(e)
+            time.sleep(self.period)
+
+    def mark(self, t0, t1):
+        self.window = (t0, t1)
 
     def __exit__(self, *a):
-        if self.proc:
-            self.proc.terminate()
+        if self.err is None or hasattr(self, "stop"):
             try:
-                self.proc.wait(timeout=5)
+                self.stop.set()
+                self.thread.join(timeout=2)
             except Exception:
-                self.proc.kill()
+                pass
 
     def summary(self):
         if not self.samples:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
-        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i] == "Active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(self.samples)}
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["no samples: " + str(self.err)]}
+        t0, t1 = self.window or (self.samples[0][0], self.samples[-1][0])
+        inside = [s for s in self.samples if t0 <= s[0] <= t1] or \
+            sorted(self.samples, key=lambda s: min(abs(s[0] - t0), abs(s[0] - t1)))[:3]
+        mask = 0
+        for s in inside:
+            mask |= int(s[2])
+        reasons = [name for name, attr in self.REASONS if mask & getattr(self.nv, attr)]
+        return {"sm_mhz": statistics.median(s[1] for s in inside), "sm_max_mhz": self.max_mhz,
+                "reasons": reasons, "samples": len(inside)}
 
 
 def dist_setup():
@@ -192,6 +210,7 @@ def main():
     ap.add_argument("--impl", default="fks", choices=["fks", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=1 << 24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-search-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=N_KEYS)
     args = ap.parse_args()
     world, rank, local = dist_setup()
@@ -258,11 +277,14 @@ def main():
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
+        time.sleep(0.05)
+        h0 = time.perf_counter()
         t_start.record(stream)
         for _ in range(args.steps):
             step(True)
         t_end.record(stream)
         torch.cuda.synchronize()
+        clk.mark(h0, time.perf_counter())
         if world > 1:
             dist.barrier()
     launches = F.fks_kernel_launches() - launches0
@@ -373,6 +395,27 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
+    # ---- reference point: the search-based map (sort + binary search) on the same data
+    if not args.no_search_baseline:
+        sb, sl = [], []
+        for i in range(4):
+            a0, a1, a2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            a0.record(stream)
+            sm = F.fks_sortmap_build(keys, vals)
+            a1.record(stream)
+            F.fks_sortmap_lookup(sm, queries, out, found, -1)
+            a2.record(stream)
+            torch.cuda.synchronize()
+            if i >= 1:
+                sb.append(a0.elapsed_time(a1))
+                sl.append(a1.elapsed_time(a2))
+            del sm
+        assert np.array_equal(found.cpu().numpy(), w.expect_found)
+        line["search_baseline"] = {
+            "what": "GPU LSD radix sort of (key, value) + binary-search lookup, same data",
+            "build_ms": med(sb), "lookup_ms": med(sl),
+            "build_keys_per_s": n / (med(sb) / 1e3), "lookups_per_s": nq / (med(sl) / 1e3),
+            "fks_speedup_build": med(sb) / med(build_ms), "fks_speedup_lookup": med(sl) / lk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import multiprocessing as mp
         ctx = mp.get_context("spawn")

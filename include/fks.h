@@ -43,6 +43,7 @@ struct CUstream_st;
 typedef struct CUstream_st* fks_stream_t; /* identical to cudaStream_t */
 
 typedef struct fks_map* fks_map_t;       /* one map                     */
+typedef struct fks_sortmap* fks_sortmap_t; /* sorted-array map (comparison point) */
 typedef struct fks_mapset* fks_mapset_t; /* maps built by one batched call */
 
 typedef enum {
@@ -219,6 +220,20 @@ fks_status fks_build_u64_noalloc(const uint64_t* keys, const void* vals, fks_val
                                  uint64_t n, uint64_t seed, const fks_build_opts* opts,
                                  uint64_t* desc_out, void* slots_out, uint64_t slot_capacity,
                                  fks_map_info_t* h_info, fks_stream_t stream);
+
+/* ------------------------------------------------------------------ search-based map
+ * The comparison point of the paper's evaluation (mk_arraymap, Sec. 3.4;
+ * Table 1 "binary search"): the pairs sorted by key (here an LSD radix
+ * sort, stable, 8 passes of 8 bits) and lookups by binary search.
+ * fks_sortmap_build does not block; keys are assumed distinct (a lookup of
+ * a repeated key returns the value of its first sorted occurrence). */
+fks_status fks_sortmap_build(const uint64_t* keys, const void* vals, fks_val_type val_type, uint64_t n,
+                             const fks_allocator* alloc, fks_stream_t stream, fks_sortmap_t* out);
+fks_status fks_sortmap_lookup(fks_sortmap_t map, const uint64_t* q, uint64_t nq, void* out_vals,
+                              uint8_t* out_found, int64_t absent, fks_stream_t stream);
+/* sorted keys and their values (int64) to host memory; synchronises */
+fks_status fks_sortmap_export(fks_sortmap_t map, uint64_t* h_keys, int64_t* h_vals, fks_stream_t stream);
+void fks_sortmap_destroy(fks_sortmap_t map);
 
 /* ------------------------------------------------------------------ tables
  * fks_map_info -- sizes and build statistics (host struct). */

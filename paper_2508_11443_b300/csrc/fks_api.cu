@@ -196,6 +196,16 @@ struct fks_mapset {
   Alloc alloc{nullptr};
 };
 
+struct fks_sortmap {
+  fks_val_type vt = FKS_VAL_I64;
+  uint64_t n = 0;
+  uint64_t* keys = nullptr;  // sorted
+  uint64_t* vals = nullptr;  // int64 words
+  void* block = nullptr;
+  size_t block_bytes = 0;
+  Alloc alloc{nullptr};
+};
+
 static LookupMap lookup_view(const fks_map& m) {
   LookupMap L;
   L.desc = m.desc;
@@ -809,6 +819,75 @@ void fks_mapset_destroy(fks_mapset_t set) {
   if (set->d_table) set->alloc.put(set->d_table, sizeof(LookupMap) * set->maps.size(), nullptr);
   if (set->block) set->alloc.put(set->block, set->block_bytes, nullptr);
   delete set;
+}
+
+fks_status fks_sortmap_build(const uint64_t* keys, const void* vals, fks_val_type val_type, uint64_t n,
+                             const fks_allocator* alloc, fks_stream_t stream, fks_sortmap_t* out) {
+  if (!out) return fail(FKS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!keys || !vals || n == 0 || n >= (1ull << 32) || (val_type != FKS_VAL_I32 && val_type != FKS_VAL_I64))
+    return fail(FKS_ERR_INVALID_ARG, "fks_sortmap_build: bad arguments");
+  sm_count();
+  Alloc A(alloc);
+  const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const size_t bytes = 16 * n;
+  uint8_t* block = static_cast<uint8_t*>(A.get(bytes, st));
+  if (!block) return fail(FKS_ERR_OUT_OF_MEMORY, "fks_sortmap_build: tables");
+  const size_t sbytes = sort_scratch_bytes(n) + (val_type == FKS_VAL_I32 ? 8 * n : 0);
+  uint8_t* scr = static_cast<uint8_t*>(A.get(sbytes, st));
+  if (!scr) {
+    A.put(block, bytes, st);
+    return fail(FKS_ERR_OUT_OF_MEMORY, "fks_sortmap_build: scratch");
+  }
+  const uint64_t* v64 = static_cast<const uint64_t*>(vals);
+  cudaError_t e = cudaSuccess;
+  if (val_type == FKS_VAL_I32) {
+    uint64_t* wide = reinterpret_cast<uint64_t*>(scr + sort_scratch_bytes(n));
+    e = launch_widen_i32(static_cast<const int32_t*>(vals), n, wide, st);
+    v64 = wide;
+  }
+  fks_sortmap* m = new fks_sortmap();
+  m->vt = val_type;
+  m->n = n;
+  m->keys = reinterpret_cast<uint64_t*>(block);
+  m->vals = m->keys + n;
+  m->block = block;
+  m->block_bytes = bytes;
+  m->alloc = A;
+  if (e == cudaSuccess) e = launch_sort_pairs(keys, v64, n, m->keys, m->vals, scr, st);
+  A.put(scr, sbytes, st);
+  if (e != cudaSuccess) {
+    fks_sortmap_destroy(m);
+    return cuda_fail(e, "fks_sortmap_build");
+  }
+  *out = m;
+  return FKS_OK;
+}
+
+fks_status fks_sortmap_lookup(fks_sortmap_t map, const uint64_t* q, uint64_t nq, void* out_vals,
+                              uint8_t* out_found, int64_t absent, fks_stream_t stream) {
+  if (!map) return fail(FKS_ERR_INVALID_ARG, "fks_sortmap_lookup: NULL map");
+  if (nq == 0) return FKS_OK;
+  if (!q || (map->vt == FKS_VAL_I32 && (absent < INT32_MIN || absent > INT32_MAX)))
+    return fail(FKS_ERR_INVALID_ARG, "fks_sortmap_lookup: bad arguments");
+  FKS_CUDA(launch_sorted_search(map->keys, map->vals, map->n, q, nq, out_vals, map->vt == FKS_VAL_I64, out_found,
+                                absent, sm_count(), reinterpret_cast<cudaStream_t>(stream)));
+  return FKS_OK;
+}
+
+fks_status fks_sortmap_export(fks_sortmap_t map, uint64_t* h_keys, int64_t* h_vals, fks_stream_t stream) {
+  if (!map) return fail(FKS_ERR_INVALID_ARG, "fks_sortmap_export: NULL map");
+  const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (h_keys) FKS_CUDA(cudaMemcpyAsync(h_keys, map->keys, 8 * map->n, cudaMemcpyDeviceToHost, st));
+  if (h_vals) FKS_CUDA(cudaMemcpyAsync(h_vals, map->vals, 8 * map->n, cudaMemcpyDeviceToHost, st));
+  FKS_CUDA(cudaStreamSynchronize(st));
+  return FKS_OK;
+}
+
+void fks_sortmap_destroy(fks_sortmap_t map) {
+  if (!map) return;
+  map->alloc.put(map->block, map->block_bytes, nullptr);
+  delete map;
 }
 
 const char* fks_status_str(fks_status status) { return status_name(status); }

@@ -430,18 +430,24 @@ __device__ __noinline__ void count_global(const PassDev& p, const MapRegs& M, ui
   }
 }
 
-// Decoupled look-back by one warp: exclusive slot prefix of partition gp
-// within its map, 32 predecessors per step.  Every wait is bounded.
-__device__ uint64_t look_back_warp(const PassDev& p, uint32_t gp, uint32_t first, uint64_t agg,
+// Decoupled look-back, in two halves so that the wait can be deferred.
+// publish_aggregate (one thread): make this partition's slot count visible
+// (the first partition of a map publishes its inclusive prefix at once).
+__device__ __forceinline__ void publish_aggregate(const PassDev& p, uint32_t gp, uint32_t first,
+                                                  uint64_t agg) {
+  if (p.cfg.hold_first && gp == 0) return;
+  st_relaxed(p.lookback + gp, (gp == first ? kLbFlagP : kLbFlagA) | sat(agg));
+}
+
+// resolve_prefix (one warp): exclusive slot prefix of partition gp within
+// its map, 32 predecessors per step, then publish the inclusive prefix.
+// Every wait is bounded by cfg.spin_limit polls.
+__device__ uint64_t resolve_prefix(const PassDev& p, uint32_t gp, uint32_t first, uint64_t agg,
                                    bool* timed_out) {
   const uint32_t lane = lane_id();
   const bool hold = p.cfg.hold_first && gp == 0;
   *timed_out = false;
-  if (gp == first) {
-    if (lane == 0 && !hold) st_relaxed(p.lookback + gp, kLbFlagP | sat(agg));
-    return 0;
-  }
-  if (lane == 0 && !hold) st_relaxed(p.lookback + gp, kLbFlagA | sat(agg));
+  if (gp == first) return 0;
   uint64_t excl = 0;
   int64_t hi = int64_t(gp) - 1;
   uint32_t polls = 0, ns = 32;
@@ -475,6 +481,24 @@ __device__ uint64_t look_back_warp(const PassDev& p, uint32_t gp, uint32_t first
   }
   if (lane == 0 && !hold) st_relaxed(p.lookback + gp, kLbFlagP | sat(excl + agg));
   return excl;
+}
+
+// Warp 0: resolve the prefix and record the partition's outcome in ctl and
+// in the map's status.
+__device__ void finish_prefix(const PassDev& p, const MapRegs& M, uint32_t gp, uint32_t j, uint64_t Sp,
+                              PartCtl& ctl) {
+  bool to = false;
+  const uint64_t excl = resolve_prefix(p, gp, M.part_begin, Sp, &to);
+  if (threadIdx.x == 0) {
+    const uint64_t incl = excl + Sp;
+    ctl.excl = excl;
+    ctl.skip = (to || incl > M.slot_cap) ? 1u : 0u;
+    if (to) atomicExch(&p.status[j].timeout, 1u);
+    if (incl > M.slot_cap) atomicExch(&p.status[j].reseed, 1u);
+    if (gp + 1 == M.part_end) p.status[j].S = incl;
+    atomicMax(&p.status[j].max_s, ctl.maxs);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&p.status[j].nonempty), (unsigned long long)ctl.nonempty);
+  }
 }
 
 // Equal keys of two members: u64 maps compare keys; string maps compare bytes.
@@ -819,22 +843,14 @@ __global__ void __launch_bounds__(kPartThreads, PW == 1 ? 2 : 1) k_part_build(Pa
     scan_buckets(cnt, gst, soff, ctl);
     const uint64_t Sp = ctl.Spart;
     const bool owner_mode = Sp <= kOwnerCap;
-    // warp 0: slot prefix of this partition (look-back); the other warps
-    // group the keys meanwhile
+    // The slot prefix of this partition (look-back across partitions) is
+    // needed only by the write-out: publish the aggregate now and resolve
+    // the prefix after the search, unless the partition writes its slots
+    // directly (oversized slot image) or is deferred to the overflow kernel.
+    const bool early = overflow || !owner_mode;
     if (t < 32) {
-      bool to = false;
-      const uint64_t excl = look_back_warp(p, gp, M.part_begin, Sp, &to);
-      if (t == 0) {
-        const uint64_t incl = excl + Sp;
-        ctl.excl = excl;
-        ctl.skip = (to || incl > M.slot_cap) ? 1u : 0u;
-        if (to) atomicExch(&p.status[j].timeout, 1u);
-        if (incl > M.slot_cap) atomicExch(&p.status[j].reseed, 1u);
-        if (gp + 1 == M.part_end) p.status[j].S = incl;
-        atomicMax(&p.status[j].max_s, ctl.maxs);
-        atomicAdd(reinterpret_cast<unsigned long long*>(&p.status[j].nonempty),
-                  (unsigned long long)ctl.nonempty);
-      }
+      if (t == 0) publish_aggregate(p, gp, M.part_begin, Sp);
+      if (early) finish_prefix(p, M, gp, j, Sp, ctl);
     }
     if (!overflow) {
 #pragma unroll
@@ -856,7 +872,7 @@ __global__ void __launch_bounds__(kPartThreads, PW == 1 ? 2 : 1) k_part_build(Pa
       ctl.next_gp = atomicAdd(p.ticket, 1u);
       ctl.next_issued = issue_stage<PW>(p, ctl.next_gp, raw_key, raw_pay, &bar);
     }
-    if (ctl.skip) {
+    if (early && ctl.skip) {
       __syncthreads();
       continue;
     }
@@ -872,7 +888,11 @@ __global__ void __launch_bounds__(kPartThreads, PW == 1 ? 2 : 1) k_part_build(Pa
     }
     search_partition<PW>(p, M, j, b0, nb, M.slot_base + ctl.excl, owner_mode, gkey, gpay, owner, gst,
                          soff, att, work, ctl);
-    if (!ctl.failed)
+    if (!early) {
+      if (t < 32) finish_prefix(p, M, gp, j, Sp, ctl);
+      __syncthreads();
+    }
+    if (!ctl.failed && !ctl.skip)
       write_partition<PW>(p, M, b0, nb, ctl.excl, owner_mode, gkey, gpay, owner, gst, soff, att, Sp);
     if (t == 0) flush_stats(p, j, ctl);
   }

@@ -163,4 +163,13 @@ cudaError_t launch_lookup_batched(const LookupMap* maps, uint32_t m, int strings
                                   const int64_t* qoffs, uint64_t nq, void* out, int out_i64,
                                   uint8_t* found, int64_t absent, int sms, cudaStream_t stream);
 
+// Search-based comparison map (fks_sort.cu).
+size_t sort_scratch_bytes(uint64_t n);
+cudaError_t launch_sort_pairs(const uint64_t* keys, const uint64_t* vals, uint64_t n, uint64_t* kout,
+                              uint64_t* vout, void* scratch, cudaStream_t st);
+cudaError_t launch_widen_i32(const int32_t* in, uint64_t n, uint64_t* out, cudaStream_t st);
+cudaError_t launch_sorted_search(const uint64_t* keys, const uint64_t* vals, uint64_t n, const uint64_t* q,
+                                 uint64_t nq, void* out, int out_i64, uint8_t* found, int64_t absent, int sms,
+                                 cudaStream_t st);
+
 }  // namespace fks

@@ -1,0 +1,267 @@
+// fks_sort.cu -- the search-based map the paper compares against
+// (mk_arraymap, Sec. 3.4): keys sorted together with their values, lookups
+// by binary search returning the index or "absent".  The paper sorts with a
+// comparison merge sort because its key abstraction offers no digits; uint64
+// keys do, so this uses a least-significant-digit radix sort, 8 passes of 8
+// bits, each pass stable:
+//   count   per tile of kSortTile keys, a shared histogram of the digit
+//   scan    exclusive scan of the digit-major histogram (device wide)
+//   scatter per tile, warp-stable ranks (__match_any_sync within a warp,
+//           warps in order), then each key to its digit's next position
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fks_internal.cuh"
+
+namespace fks {
+namespace {
+
+constexpr uint32_t kSortTile = 2048;
+constexpr int kSortThreads = 256;  // 8 warps x 256 keys each, 32 per round
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr uint32_t kPerWarp = kSortTile / kSortWarps;
+constexpr uint32_t kRounds = kPerWarp / 32;
+constexpr uint32_t kScanItems = 8192;
+constexpr int kScanThreads = 512;
+
+__device__ __forceinline__ uint32_t lane() { return threadIdx.x & 31u; }
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_count(const uint64_t* __restrict__ keys, uint64_t n,
+                                                             uint32_t shift, uint32_t tiles,
+                                                             uint32_t* __restrict__ hist) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const uint64_t t0 = uint64_t(blockIdx.x) * kSortTile;
+  for (uint32_t i = threadIdx.x; i < kSortTile; i += kSortThreads) {
+    if (t0 + i < n) atomicAdd(h + uint32_t((__ldcs(keys + t0 + i) >> shift) & 255u), 1u);
+  }
+  __syncthreads();
+  hist[uint64_t(threadIdx.x) * tiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint64_t* __restrict__ kin,
+                                                               const uint64_t* __restrict__ vin,
+                                                               uint64_t* __restrict__ kout,
+                                                               uint64_t* __restrict__ vout, uint64_t n,
+                                                               uint32_t shift, uint32_t tiles,
+                                                               const uint32_t* __restrict__ hist) {
+  __shared__ uint32_t cnt[kSortWarps][256];
+  const uint32_t w = threadIdx.x >> 5;
+  for (uint32_t d = lane(); d < 256; d += 32) cnt[w][d] = 0;
+  __syncwarp();
+  const uint64_t base = uint64_t(blockIdx.x) * kSortTile + uint64_t(w) * kPerWarp;
+  uint64_t k[kRounds], v[kRounds];
+  uint32_t dg[kRounds], rk[kRounds];
+#pragma unroll
+  for (uint32_t r = 0; r < kRounds; ++r) {
+    const uint64_t e = base + r * 32 + lane();
+    const bool ok = e < n;
+    k[r] = ok ? __ldcs(kin + e) : 0;
+    v[r] = ok ? __ldcs(vin + e) : 0;
+    dg[r] = ok ? uint32_t((k[r] >> shift) & 255u) : 256u;
+  }
+#pragma unroll
+  for (uint32_t r = 0; r < kRounds; ++r) {
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, dg[r]);
+    const uint32_t leader = __ffs(peers) - 1;
+    const uint32_t before = dg[r] < 256u ? cnt[w][dg[r]] : 0u;
+    rk[r] = before + __popc(peers & lanemask_lt());
+    __syncwarp();
+    if (lane() == leader && dg[r] < 256u) cnt[w][dg[r]] = before + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // per digit, the keys of earlier warps of this tile come first
+  if (threadIdx.x < 256) {
+    uint32_t run = hist[uint64_t(threadIdx.x) * tiles + blockIdx.x];
+    for (int ww = 0; ww < kSortWarps; ++ww) {
+      const uint32_t c = cnt[ww][threadIdx.x];
+      cnt[ww][threadIdx.x] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (uint32_t r = 0; r < kRounds; ++r) {
+    if (dg[r] < 256u) {
+      const uint32_t dst = cnt[w][dg[r]] + rk[r];
+      kout[dst] = k[r];
+      vout[dst] = v[r];
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_sum_blocks(const uint32_t* in, uint64_t n, uint32_t* sums) {
+  __shared__ uint32_t ws[kScanThreads / 32];
+  const uint64_t b0 = uint64_t(blockIdx.x) * kScanItems;
+  uint32_t v = 0;
+  for (uint64_t i = b0 + threadIdx.x; i < min(n, b0 + kScanItems); i += kScanThreads) v += in[i];
+  v = __reduce_add_sync(0xFFFFFFFFu, v);
+  if (lane() == 0) ws[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t tot = 0;
+    for (int i = 0; i < kScanThreads / 32; ++i) tot += ws[i];
+    sums[blockIdx.x] = tot;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_scan_block_sums(uint32_t* sums, uint32_t nb) {
+  __shared__ uint32_t ws[32];
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (uint32_t c0 = 0; c0 < nb; c0 += 1024) {
+    const uint32_t i = c0 + threadIdx.x;
+    const uint32_t v = i < nb ? sums[i] : 0u;
+    uint32_t inc = v;
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, d);
+      if (lane() >= uint32_t(d)) inc += y;
+    }
+    if (lane() == 31) ws[threadIdx.x >> 5] = inc;
+    __syncthreads();
+    uint32_t b = carry;
+    for (uint32_t q = 0; q < (threadIdx.x >> 5); ++q) b += ws[q];
+    if (i < nb) sums[i] = b + inc - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry = b + inc;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(uint32_t* data, uint64_t n, const uint32_t* sums) {
+  __shared__ uint32_t ws[kScanThreads / 32];
+  constexpr uint32_t kPer = kScanItems / kScanThreads;
+  const uint64_t b0 = uint64_t(blockIdx.x) * kScanItems + uint64_t(threadIdx.x) * kPer;
+  uint32_t v[kPer], sum = 0;
+#pragma unroll
+  for (uint32_t q = 0; q < kPer; ++q) {
+    v[q] = b0 + q < n ? data[b0 + q] : 0u;
+    sum += v[q];
+  }
+  uint32_t inc = sum;
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, d);
+    if (lane() >= uint32_t(d)) inc += y;
+  }
+  if (lane() == 31) ws[threadIdx.x >> 5] = inc;
+  __syncthreads();
+  uint32_t run = sums[blockIdx.x];
+  for (uint32_t q = 0; q < (threadIdx.x >> 5); ++q) run += ws[q];
+  run += inc - sum;
+#pragma unroll
+  for (uint32_t q = 0; q < kPer; ++q) {
+    if (b0 + q < n) data[b0 + q] = run;
+    run += v[q];
+  }
+}
+
+// Binary search (lower bound) of each needle; index or absent (Sec. 3.4:
+// binary_search returns -1 for a needle that is not there).
+template <bool kI64>
+__global__ void __launch_bounds__(256) k_search(const uint64_t* __restrict__ keys, const uint64_t* __restrict__ vals,
+                                                uint64_t n, const uint64_t* __restrict__ q, uint64_t nq,
+                                                void* __restrict__ out, uint8_t* __restrict__ found,
+                                                int64_t absent) {
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < nq; i += stride) {
+    const uint64_t x = __ldcs(q + i);
+    uint64_t lo = 0, len = n;
+    while (len > 0) {
+      const uint64_t half = len >> 1;
+      if (__ldg(keys + lo + half) < x) {
+        lo += half + 1;
+        len -= half + 1;
+      } else {
+        len = half;
+      }
+    }
+    const bool hit = lo < n && __ldg(keys + lo) == x;
+    const int64_t v = hit ? int64_t(__ldg(vals + lo)) : absent;
+    if (out) {
+      if (kI64) static_cast<int64_t*>(out)[i] = v;
+      else static_cast<int32_t*>(out)[i] = int32_t(v);
+    }
+    if (found) found[i] = uint8_t(hit);
+  }
+}
+
+__global__ void k_widen_i32(const int32_t* __restrict__ in, uint64_t n, uint64_t* __restrict__ out) {
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride)
+    out[i] = uint64_t(int64_t(in[i]));
+}
+
+cudaError_t scan(uint32_t* data, uint64_t n, uint32_t* sums, cudaStream_t st) {
+  const uint32_t nb = uint32_t((n + kScanItems - 1) / kScanItems);
+  k_sum_blocks<<<nb, kScanThreads, 0, st>>>(data, n, sums);
+  k_scan_block_sums<<<1, 1024, 0, st>>>(sums, nb);
+  k_scan_apply<<<nb, kScanThreads, 0, st>>>(data, n, sums);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t sort_scratch_bytes(uint64_t n) {
+  const uint64_t tiles = (n + kSortTile - 1) / kSortTile;
+  const uint64_t hist = 256 * tiles;
+  return 2 * 8 * n + 4 * hist + 4 * (hist / kScanItems + 2) + 1024;
+}
+
+// Sort (keys, vals) ascending by key into (kout, vout); vals are 64-bit
+// words.  scratch holds sort_scratch_bytes(n).
+cudaError_t launch_sort_pairs(const uint64_t* keys, const uint64_t* vals, uint64_t n, uint64_t* kout,
+                              uint64_t* vout, void* scratch, cudaStream_t st) {
+  const uint32_t tiles = uint32_t((n + kSortTile - 1) / kSortTile);
+  uint64_t* tk = static_cast<uint64_t*>(scratch);
+  uint64_t* tv = tk + n;
+  uint32_t* hist = reinterpret_cast<uint32_t*>(tv + n);
+  uint32_t* sums = hist + 256ull * tiles;
+  const uint64_t* ik = keys;
+  const uint64_t* iv = vals;
+  // 8 passes; even passes write (tk, tv), odd passes (kout, vout): the last
+  // pass lands in kout/vout
+  for (uint32_t pass = 0; pass < 8; ++pass) {
+    uint64_t* ok = (pass & 1) ? kout : tk;
+    uint64_t* ov = (pass & 1) ? vout : tv;
+    const uint32_t shift = 8 * pass;
+    k_sort_count<<<tiles, kSortThreads, 0, st>>>(ik, n, shift, tiles, hist);
+    cudaError_t e = scan(hist, 256ull * tiles, sums, st);
+    if (e != cudaSuccess) return e;
+    k_sort_scatter<<<tiles, kSortThreads, 0, st>>>(ik, iv, ok, ov, n, shift, tiles, hist);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    ik = ok;
+    iv = ov;
+  }
+  note_launches(8 * 5);
+  return cudaSuccess;
+}
+
+cudaError_t launch_widen_i32(const int32_t* in, uint64_t n, uint64_t* out, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_widen_i32<<<1184, 256, 0, st>>>(in, n, out);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sorted_search(const uint64_t* keys, const uint64_t* vals, uint64_t n, const uint64_t* q,
+                                 uint64_t nq, void* out, int out_i64, uint8_t* found, int64_t absent, int sms,
+                                 cudaStream_t st) {
+  if (nq == 0) return cudaSuccess;
+  uint64_t blocks = (nq + 255) / 256;
+  const uint64_t cap = uint64_t(sms) * 8;
+  if (blocks > cap) blocks = cap;
+  if (out_i64) k_search<true><<<unsigned(blocks), 256, 0, st>>>(keys, vals, n, q, nq, out, found, absent);
+  else k_search<false><<<unsigned(blocks), 256, 0, st>>>(keys, vals, n, q, nq, out, found, absent);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace fks

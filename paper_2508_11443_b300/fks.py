@@ -90,6 +90,14 @@ def lib():
         L.fks_status_str.restype = ctypes.c_char_p
         L.fks_last_error.argtypes = []
         L.fks_last_error.restype = ctypes.c_char_p
+        L.fks_sortmap_build.argtypes = [vp, vp, ctypes.c_int, u64, vp, vp, ctypes.POINTER(vp)]
+        L.fks_sortmap_build.restype = st
+        L.fks_sortmap_lookup.argtypes = [vp, vp, u64, vp, vp, i64, vp]
+        L.fks_sortmap_lookup.restype = st
+        L.fks_sortmap_export.argtypes = [vp, vp, vp, vp]
+        L.fks_sortmap_export.restype = st
+        L.fks_sortmap_destroy.argtypes = [vp]
+        L.fks_sortmap_destroy.restype = None
         L.fks_profile_enable.argtypes = [ctypes.c_int]
         L.fks_profile_enable.restype = None
         L.fks_last_build_profile.argtypes = [ctypes.POINTER(fks_build_profile)]
@@ -266,6 +274,38 @@ def fks_map_export(m: Map, stream=None):
     if ctx is not None:
         ctx = ctx[: info.context_bytes]
     return desc, slots, ctx
+
+
+class SortMap:
+    """Owning handle of a sorted-array map (the search-based comparison)."""
+
+    def __init__(self, handle: int, n: int):
+        self.handle, self.n = handle, n
+
+    def __del__(self):
+        if self.handle and _lib is not None:
+            _lib.fks_sortmap_destroy(self.handle)
+            self.handle = None
+
+
+def fks_sortmap_build(keys, vals, stream=None) -> SortMap:
+    h = ctypes.c_void_p()
+    _check(lib().fks_sortmap_build(_ptr(keys), _ptr(vals), _val_type(vals), keys.numel(), None,
+                                   _stream(stream), ctypes.byref(h)))
+    return SortMap(h.value, keys.numel())
+
+
+def fks_sortmap_lookup(m: SortMap, q, out_vals=None, out_found=None, absent: int = -1, stream=None):
+    _check(lib().fks_sortmap_lookup(m.handle, _ptr(q), q.numel(), _ptr(out_vals), _ptr(out_found),
+                                    absent, _stream(stream)))
+
+
+def fks_sortmap_export(m: SortMap, stream=None):
+    k = np.empty(m.n, np.uint64)
+    v = np.empty(m.n, np.int64)
+    _check(lib().fks_sortmap_export(m.handle, k.ctypes.data_as(ctypes.c_void_p),
+                                    v.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+    return k, v
 
 
 def fks_status_str(status: int) -> str:
