@@ -117,30 +117,61 @@ class ClockSampler:
             self.stop = threading.Event()
             self.thread = threading.Thread(target=self._run, daemon=True)
             self.thread.start()
-        except Exception as e:  # no NVML: report it, keep running
+        except Exception as e:  # no NVML binding: nvidia-smi queries instead
             self.err = repr(e)
+            self._start_smi()
         return self
 
-    def _run(self):
-        nv, h = self.nv, self.h
-        while not self.stop.is_set():
+    # bit values of the NVML clock-event reasons, for the nvidia-smi fallback
+    SMI_BITS = {"hw_slowdown": 0x8, "hw_thermal_slowdown": 0x40, "sw_thermal_slowdown": 0x20,
+                "sw_power_cap": 0x4, "hw_power_brake": 0x80}
+
+    def _start_smi(self):
+        import subprocess
+        q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap,clocks_event_reasons.hw_power_brake_slowdown")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "10"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read_smi, daemon=True)
+            self.thread.start()
+            time.sleep(0.5)  # let nvidia-smi start before the timed region
+        except Exception as e:
+            self.err = repr(e)
+            self.proc = None
+
+    def _read_smi(self):
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap", "hw_power_brake"]
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) != 7:
+                continue
             try:
-                self.samples.append((time.perf_counter(), nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM),
-                                     nv.nvmlDeviceGetCurrentClocksEventReasons(h)))
-            except Exception as e:
-                self.err = repr(e)
-            time.sleep(self.period)
+                sm = float(parts[0])
+                self.max_mhz = float(parts[1])
+            except ValueError:
+                continue
+            mask = 0
+            for name, val in zip(names, parts[2:]):
+                if val == "Active":
+                    mask |= self.SMI_BITS[name]
+            self.samples.append((time.perf_counter(), sm, mask))
 
     def mark(self, t0, t1):
         self.window = (t0, t1)
 
     def __exit__(self, *a):
-        if self.err is None or hasattr(self, "stop"):
+        if hasattr(self, "stop"):
+            self.stop.set()
+            self.thread.join(timeout=2)
+        if getattr(self, "proc", None) is not None:
+            self.proc.terminate()
             try:
-                self.stop.set()
-                self.thread.join(timeout=2)
+                self.proc.wait(timeout=5)
             except Exception:
-                pass
+                self.proc.kill()
 
     def summary(self):
         if not self.samples:
@@ -151,7 +182,7 @@ class ClockSampler:
         mask = 0
         for s in inside:
             mask |= int(s[2])
-        reasons = [name for name, attr in self.REASONS if mask & getattr(self.nv, attr)]
+        reasons = [name for name, _ in self.REASONS if mask & self.SMI_BITS[name]]
         return {"sm_mhz": statistics.median(s[1] for s in inside), "sm_max_mhz": self.max_mhz,
                 "reasons": reasons, "samples": len(inside)}
 
@@ -202,6 +233,70 @@ def run_reference(args, world, rank):
     print(json.dumps(line))
 
 
+def run_serving(args, F, W, torch):
+    """Config 5: a Poisson stream of build and lookup requests (90 % lookups of
+    log-uniform size in [1, 2^16], 80 % hits; 10 % builds, half uint64 maps of
+    log-uniform size in [2^10, 2^22], half string maps in [2^10, 2^20]) over
+    maps resident under a 40 GB budget with LRU eviction, after 64 prefill
+    builds.  The per-call server's saturation throughput mu is measured with
+    every request arriving at once; both servers then replay the same stream
+    at lambda = rho * mu.  Latency: submission to completion seen on the host."""
+    strings = W.string_workload(1 << 20, 1 << 20, 0.0, seed=55)
+    plan = W.serving_plan(args.serve_requests, 77, 40 << 30, strings.offs)
+    data = W.ServeData(plan, seed=78, strings=strings)
+    exp_found = None
+    pre = plan.prefill
+
+    def once(mode, arrival):
+        srv = F.fks_server_create(memory_budget=plan.budget, max_maps=int(plan.map_id.max()) + 1, mode=mode)
+        # prefill builds (outside the clock), then the timed stream
+        F.fks_server_replay(srv, data.reqs, np.zeros(pre))
+        F.fks_server_drain(srv)
+        import ctypes
+        stream_reqs = (F.fks_request * (plan.kind.size - pre)).from_address(
+            ctypes.addressof(data.reqs) + pre * ctypes.sizeof(F.fks_request))
+        tickets = F.fks_server_replay(srv, stream_reqs, arrival)
+        F.fks_server_drain(srv)
+        res = [F.fks_server_wait(srv, int(t)) for t in tickets]
+        st = F.fks_server_stats(srv)
+        srv.close()
+        lat = np.array([l for _, l in res])
+        ok = np.array([s == F.FKS_OK for s, _ in res])
+        kinds = plan.kind[pre:]
+        span = (max(arrival[-1], 0) + 0.0) / 1e6
+        t_last = max(arrival[i] + lat[i] for i in range(lat.size)) / 1e6
+        return {"p50_us": float(np.percentile(lat, 50)), "p99_us": float(np.percentile(lat, 99)),
+                "lookup_p50_us": float(np.percentile(lat[kinds == 1], 50)),
+                "lookup_p99_us": float(np.percentile(lat[kinds == 1], 99)),
+                "build_p50_us": float(np.percentile(lat[kinds == 0], 50)),
+                "build_p99_us": float(np.percentile(lat[kinds == 0], 99)),
+                "throughput_req_per_s": lat.size / t_last, "queries_per_s": float(plan.nq[pre:].sum()) / t_last,
+                "failed": int((~ok).sum()), "lookup_batches": int(st.batches), "evictions": int(st.evictions),
+                "peak_resident_gb": st.peak_resident_bytes / 1e9}
+
+    m = plan.kind.size - pre
+    sat = once(F.FKS_SERVE_PER_CALL, np.zeros(m))
+    mu = sat["throughput_req_per_s"]
+    out = {"requests": m, "prefill_builds": pre, "budget_gb": 40, "mu_per_call_req_per_s": mu,
+           "rho": args.serve_rho, "rate_req_per_s": args.serve_rho * mu}
+    arrival = W.poisson_arrivals_us(m, args.serve_rho * mu, 5)
+    out["per_call"] = once(F.FKS_SERVE_PER_CALL, arrival)
+    out["batched"] = once(F.FKS_SERVE_BATCHED, arrival)
+    # the batched run's results against the stream's truth
+    f = data.found.cpu().numpy()
+    looks = np.nonzero(plan.kind == 1)[0]
+    want = np.concatenate([data.u_hit.cpu().numpy().astype(np.uint8) if data.u_index else np.zeros(0, np.uint8),
+                           data.s_hit.cpu().numpy().astype(np.uint8) if data.s_index else np.zeros(0, np.uint8)])
+    got = np.concatenate([np.concatenate([f[data.out_start[r]:data.out_start[r] + plan.nq[r]]
+                                          for r in looks if plan.key_kind[r] == k] or [np.zeros(0, np.uint8)])
+                          for k in (0, 1)])
+    out["batched_results_match_truth"] = bool(np.array_equal(got, want))
+    out["p99_ratio_per_call_over_batched"] = out["per_call"]["p99_us"] / max(out["batched"]["p99_us"], 1e-9)
+    out["throughput_ratio_batched_over_per_call"] = (out["batched"]["throughput_req_per_s"] /
+                                                    out["per_call"]["throughput_req_per_s"])
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -211,6 +306,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=1 << 24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-search-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=20000)
+    ap.add_argument("--serve-rho", type=float, default=0.8)
     ap.add_argument("--n", type=int, default=N_KEYS)
     args = ap.parse_args()
     world, rank, local = dist_setup()
@@ -416,6 +513,9 @@ def main():
             "build_ms": med(sb), "lookup_ms": med(sl),
             "build_keys_per_s": n / (med(sb) / 1e3), "lookups_per_s": nq / (med(sl) / 1e3),
             "fks_speedup_build": med(sb) / med(build_ms), "fks_speedup_lookup": med(sl) / lk}
+    # ---- serving stream (config 5): continuous batching against per-call launches
+    if args.serve_requests > 0:
+        line["serving"] = run_serving(args, F, W, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import multiprocessing as mp
         ctx = mp.get_context("spawn")

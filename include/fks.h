@@ -235,6 +235,89 @@ fks_status fks_sortmap_lookup(fks_sortmap_t map, const uint64_t* q, uint64_t nq,
 fks_status fks_sortmap_export(fks_sortmap_t map, uint64_t* h_keys, int64_t* h_vals, fks_stream_t stream);
 void fks_sortmap_destroy(fks_sortmap_t map);
 
+/* ------------------------------------------------------------------ serving
+ * A request loop over resident maps: build and lookup requests are
+ * submitted as they arrive (from any thread) and complete asynchronously.
+ *   - Builds are admitted in arrival order against a device-memory budget:
+ *     least-recently-used resident maps are evicted until the new map fits
+ *     (accounted size 72 B/key for uint64 maps, 136 B/key + context bytes
+ *     for string maps).  An evicted map that still has lookups in flight is
+ *     freed when they finish.  Builds run on worker threads with their own
+ *     streams.
+ *   - FKS_SERVE_BATCHED (continuous batching): every lookup whose map is
+ *     ready joins the next coalesced launch; lookups that arrive while a
+ *     batch runs go into the following one.  A lookup of a map still being
+ *     built waits for that build.
+ *   - FKS_SERVE_PER_CALL: one request at a time in arrival order, each as
+ *     its own launch followed by a synchronisation (the comparison point).
+ * Latency of a request = submission to the moment the server observed its
+ * completion on the host.  All device pointers of a request must stay valid
+ * until it completes; results are written to the request's own buffers. */
+typedef struct fks_server* fks_server_t;
+typedef enum { FKS_SERVE_BATCHED = 0, FKS_SERVE_PER_CALL = 1 } fks_serve_mode;
+typedef enum { FKS_REQ_BUILD = 0, FKS_REQ_LOOKUP = 1 } fks_request_type;
+
+typedef struct {
+  size_t struct_size;        /* sizeof(fks_server_opts)                     */
+  uint64_t memory_budget;    /* bytes of resident maps (accounted sizes)    */
+  uint32_t max_maps;         /* map ids are 0 .. max_maps-1                 */
+  uint32_t mode;             /* fks_serve_mode                              */
+  uint32_t build_workers;    /* threads running builds (default 2)          */
+  uint32_t max_batch_requests; /* lookups per coalesced launch (default 4096) */
+  uint32_t max_inflight_batches; /* coalesced launches in flight (default 2) */
+} fks_server_opts;
+
+typedef struct {
+  size_t struct_size;        /* sizeof(fks_request)                          */
+  uint32_t type;             /* fks_request_type                            */
+  uint32_t map_id;           /* build: id the new map takes; lookup: target */
+  uint32_t key_kind;         /* fks_key_kind                                */
+  uint32_t val_type;         /* fks_val_type (build)                        */
+  /* build: uint64 keys, or ctx/offs (ctx_bytes = offs[n]); device memory  */
+  const uint64_t* keys;
+  const uint8_t* ctx;
+  const int64_t* offs;
+  uint64_t ctx_bytes;
+  const void* vals;
+  uint64_t n;
+  uint64_t seed;
+  /* lookup: q (uint64) or qctx/qoffs (strings), outputs; device memory     */
+  const uint64_t* q;
+  const uint8_t* qctx;
+  const int64_t* qoffs;
+  uint64_t nq;
+  void* out_vals;            /* nullable; int32/int64 per the map           */
+  uint8_t* out_found;        /* nullable                                    */
+  int64_t absent;
+} fks_request;
+
+typedef struct {
+  uint64_t submitted, completed, builds, lookups, queries;
+  uint64_t batches;          /* lookup launches                             */
+  uint64_t evictions, rejected;
+  uint64_t resident_bytes, peak_resident_bytes;
+  double span_s;             /* first submission to last completion         */
+  double p50_us, p99_us, p999_us;              /* all requests              */
+  double lookup_p50_us, lookup_p99_us, build_p50_us, build_p99_us;
+} fks_server_stats_t;
+
+fks_status fks_server_create(const fks_server_opts* opts, fks_server_t* out);
+/* non-blocking; h_ticket identifies the request for fks_server_wait */
+fks_status fks_server_submit(fks_server_t srv, const fks_request* req, uint64_t* h_ticket);
+/* load generator: submits reqs[i] at h_arrival_us[i] microseconds after the
+ * call (spinning on the host clock); returns once all are submitted */
+fks_status fks_server_replay(fks_server_t srv, const fks_request* reqs, const double* h_arrival_us,
+                             uint64_t count, uint64_t* h_tickets);
+/* blocks until the request completed; its status and latency (us) */
+fks_status fks_server_wait(fks_server_t srv, uint64_t ticket, fks_status* h_result, double* h_latency_us);
+/* blocks until every submitted request completed */
+fks_status fks_server_drain(fks_server_t srv);
+fks_status fks_server_stats(fks_server_t srv, fks_server_stats_t* h_out);
+/* a borrowed handle of a resident map (NULL if not resident); waits for
+ * every submitted request first -- call it while no client submits */
+fks_map_t fks_server_map(fks_server_t srv, uint32_t map_id);
+void fks_server_destroy(fks_server_t srv);
+
 /* ------------------------------------------------------------------ tables
  * fks_map_info -- sizes and build statistics (host struct). */
 fks_status fks_map_info(fks_map_t map, fks_map_info_t* h_out);

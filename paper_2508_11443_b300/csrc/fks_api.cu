@@ -620,6 +620,18 @@ static fks_status build_single(const BuildIn& in, const fks_build_opts* opts,
   return FKS_OK;
 }
 
+// Lookup view of a map handle, for the serving loop (fks_serve.cu).
+namespace fks {
+bool lookup_view_of(fks_map_t m, LookupMap* out, int* strings, int* out_i64) {
+  if (!m || !m->desc) return false;
+  *out = lookup_view(*m);
+  *strings = m->kind == FKS_KEY_BYTES;
+  *out_i64 = m->vt == FKS_VAL_I64;
+  return true;
+}
+int device_sm_count() { return sm_count(); }
+}  // namespace fks
+
 // ================================================================ C ABI
 extern "C" {
 

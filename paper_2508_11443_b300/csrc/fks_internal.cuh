@@ -6,6 +6,8 @@
 
 #include "fks_device.cuh"
 
+struct fks_map;  // handle type of the C ABI (fks_api.cu)
+
 namespace fks {
 
 // Level-one buckets are processed in partitions of kB consecutive buckets.
@@ -162,6 +164,26 @@ cudaError_t launch_lookup_batched(const LookupMap* maps, uint32_t m, int strings
                                   const uint32_t* ids, const uint64_t* q, const uint8_t* qctx,
                                   const int64_t* qoffs, uint64_t nq, void* out, int out_i64,
                                   uint8_t* found, int64_t absent, int sms, cudaStream_t stream);
+
+// One lookup request of a coalesced serving batch (fks_lookup.cu).
+struct LookupReq {
+  LookupMap M;
+  const uint64_t* q;      // u64 needles
+  const uint8_t* qctx;    // string needles
+  const int64_t* qoffs;
+  void* out;              // nullable
+  uint8_t* found;         // nullable
+  int64_t absent;
+  uint64_t begin;         // first query of this request in the batch
+  uint32_t strings;
+  uint32_t out_i64;
+};
+cudaError_t launch_lookup_requests(const LookupReq* reqs, const uint64_t* begins, uint32_t nreq,
+                                   uint64_t total, int sms, cudaStream_t stream);
+
+// Host helpers of fks_api.cu used by the serving loop.
+bool lookup_view_of(struct ::fks_map* m, LookupMap* out, int* strings, int* out_i64);
+int device_sm_count();
 
 // Search-based comparison map (fks_sort.cu).
 size_t sort_scratch_bytes(uint64_t n);

@@ -258,6 +258,57 @@ __global__ void __launch_bounds__(kLookupThreads) k_lookup_batched(
   }
 }
 
+// All queries of many lookup requests (different maps, key kinds, output
+// buffers) in one launch: query i belongs to the request whose
+// [begin, begin + nq) holds it.
+__global__ void __launch_bounds__(kLookupThreads) k_lookup_requests(const LookupReq* __restrict__ reqs,
+                                                                    const uint64_t* __restrict__ begins,
+                                                                    uint32_t nreq, uint64_t total) {
+  __shared__ uint64_t sb[1025];
+  const bool cached = nreq <= 1024;
+  if (cached) {
+    for (uint32_t i = threadIdx.x; i <= nreq; i += blockDim.x) sb[i] = begins[i];
+    __syncthreads();
+  }
+  const uint64_t* b = cached ? sb : begins;
+  const uint64_t keep = policy_keep(), strm = policy_stream();
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < total; i += stride) {
+    uint32_t lo = 0, hi = nreq;
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (b[mid] <= i) lo = mid; else hi = mid;
+    }
+    const LookupReq& R = reqs[lo];
+    const uint64_t local = i - b[lo];
+    int64_t v = R.absent;
+    bool hit = false;
+    if (!R.strings) {
+      const uint64_t k = __ldcs(R.q + local);
+      const uint32_t bk = reduce32(hash32(R.M.c1, k), R.M.n);
+      const uint64_t d = ld_na_u64(R.M.desc + bk, keep);
+      const uint32_t s = desc_s(d);
+      if (s) {
+        const HashConsts c = derive(R.M.seed, R.M.round, bk, desc_attempt(d));
+        const ulonglong2 sl = ld_na_u128(R.M.slots + 2ull * (desc_off(d) + reduce32(hash32(c, k), s * s)), strm);
+        hit = sl.x == k;
+        if (hit) v = int64_t(sl.y);
+      }
+    } else {
+      const int64_t o0 = __ldg(reinterpret_cast<const long long*>(R.qoffs) + local);
+      const int64_t o1 = __ldg(reinterpret_cast<const long long*>(R.qoffs) + local + 1);
+      if (o0 >= 0 && o1 >= o0 && o1 - o0 < (int64_t(1) << 24))
+        hit = lookup_one_bytes(R.M, R.qctx + o0, uint32_t(o1 - o0), &v);
+      if (!hit) v = R.absent;
+    }
+    if (R.out) {
+      if (R.out_i64) static_cast<int64_t*>(R.out)[local] = v;
+      else static_cast<int32_t*>(R.out)[local] = int32_t(v);
+    }
+    if (R.found) R.found[local] = uint8_t(hit);
+  }
+}
+
 unsigned grid_for(uint64_t work, int sms, int per_sm) {
   uint64_t blocks = (work + kLookupThreads - 1) / kLookupThreads;
   const uint64_t cap = uint64_t(sms) * per_sm;
@@ -291,6 +342,14 @@ cudaError_t launch_lookup_bytes(const LookupMap& M, const uint8_t* qctx, const i
     k_lookup_bytes<true><<<grid, kLookupThreads, 0, stream>>>(M, qctx, qoffs, nq, out, found, absent);
   else
     k_lookup_bytes<false><<<grid, kLookupThreads, 0, stream>>>(M, qctx, qoffs, nq, out, found, absent);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lookup_requests(const LookupReq* reqs, const uint64_t* begins, uint32_t nreq,
+                                   uint64_t total, int sms, cudaStream_t stream) {
+  if (total == 0 || nreq == 0) return cudaSuccess;
+  k_lookup_requests<<<grid_for(total, sms, 8), kLookupThreads, 0, stream>>>(reqs, begins, nreq, total);
   note_launches(1);
   return cudaGetLastError();
 }

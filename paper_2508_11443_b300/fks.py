@@ -308,6 +308,130 @@ def fks_sortmap_export(m: SortMap, stream=None):
     return k, v
 
 
+# ------------------------------------------------------------------ serving
+FKS_SERVE_BATCHED, FKS_SERVE_PER_CALL = 0, 1
+FKS_REQ_BUILD, FKS_REQ_LOOKUP = 0, 1
+
+
+class fks_server_opts(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_size_t), ("memory_budget", ctypes.c_uint64),
+                ("max_maps", ctypes.c_uint32), ("mode", ctypes.c_uint32),
+                ("build_workers", ctypes.c_uint32), ("max_batch_requests", ctypes.c_uint32),
+                ("max_inflight_batches", ctypes.c_uint32)]
+
+
+class fks_request(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_size_t), ("type", ctypes.c_uint32), ("map_id", ctypes.c_uint32),
+                ("key_kind", ctypes.c_uint32), ("val_type", ctypes.c_uint32),
+                ("keys", ctypes.c_void_p), ("ctx", ctypes.c_void_p), ("offs", ctypes.c_void_p),
+                ("ctx_bytes", ctypes.c_uint64), ("vals", ctypes.c_void_p), ("n", ctypes.c_uint64),
+                ("seed", ctypes.c_uint64), ("q", ctypes.c_void_p), ("qctx", ctypes.c_void_p),
+                ("qoffs", ctypes.c_void_p), ("nq", ctypes.c_uint64), ("out_vals", ctypes.c_void_p),
+                ("out_found", ctypes.c_void_p), ("absent", ctypes.c_int64)]
+
+
+class fks_server_stats_t(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_uint64) for k in ("submitted", "completed", "builds", "lookups", "queries",
+                                                 "batches", "evictions", "rejected", "resident_bytes",
+                                                 "peak_resident_bytes")] + \
+               [(k, ctypes.c_double) for k in ("span_s", "p50_us", "p99_us", "p999_us", "lookup_p50_us",
+                                                 "lookup_p99_us", "build_p50_us", "build_p99_us")]
+
+
+def _server_lib():
+    L = lib()
+    if not getattr(L, "_server_types", False):
+        vp, u64 = ctypes.c_void_p, ctypes.c_uint64
+        L.fks_server_create.argtypes = [ctypes.POINTER(fks_server_opts), ctypes.POINTER(vp)]
+        L.fks_server_create.restype = ctypes.c_int
+        L.fks_server_submit.argtypes = [vp, ctypes.POINTER(fks_request), ctypes.POINTER(u64)]
+        L.fks_server_submit.restype = ctypes.c_int
+        L.fks_server_replay.argtypes = [vp, vp, vp, u64, vp]
+        L.fks_server_replay.restype = ctypes.c_int
+        L.fks_server_wait.argtypes = [vp, u64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+        L.fks_server_wait.restype = ctypes.c_int
+        L.fks_server_drain.argtypes = [vp]
+        L.fks_server_drain.restype = ctypes.c_int
+        L.fks_server_stats.argtypes = [vp, ctypes.POINTER(fks_server_stats_t)]
+        L.fks_server_stats.restype = ctypes.c_int
+        L.fks_server_map.argtypes = [vp, ctypes.c_uint32]
+        L.fks_server_map.restype = vp
+        L.fks_server_destroy.argtypes = [vp]
+        L.fks_server_destroy.restype = None
+        L._server_types = True
+    return L
+
+
+class Server:
+    """Owning handle of a serving loop (fks_server_*)."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    def close(self):
+        if self.handle and _lib is not None:
+            _lib.fks_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+
+def fks_server_create(memory_budget: int, max_maps: int, mode: int = FKS_SERVE_BATCHED,
+                      build_workers: int = 0, max_batch_requests: int = 0,
+                      max_inflight_batches: int = 0) -> Server:
+    o = fks_server_opts(ctypes.sizeof(fks_server_opts), memory_budget, max_maps, mode, build_workers,
+                        max_batch_requests, max_inflight_batches)
+    h = ctypes.c_void_p()
+    _check(_server_lib().fks_server_create(ctypes.byref(o), ctypes.byref(h)))
+    return Server(h.value)
+
+
+def make_request(**kw) -> fks_request:
+    r = fks_request()
+    r.struct_size = ctypes.sizeof(fks_request)
+    for k, v in kw.items():
+        setattr(r, k, v)
+    return r
+
+
+def fks_server_submit(s: Server, req: fks_request) -> int:
+    t = ctypes.c_uint64()
+    _check(_server_lib().fks_server_submit(s.handle, ctypes.byref(req), ctypes.byref(t)))
+    return t.value
+
+
+def fks_server_replay(s: Server, reqs, arrival_us: np.ndarray) -> np.ndarray:
+    """reqs: a ctypes array of fks_request; returns the tickets."""
+    arr = np.ascontiguousarray(arrival_us, np.float64)
+    tickets = np.zeros(arr.size, np.uint64)
+    _check(_server_lib().fks_server_replay(s.handle, ctypes.cast(reqs, ctypes.c_void_p),
+                                           arr.ctypes.data_as(ctypes.c_void_p), arr.size,
+                                           tickets.ctypes.data_as(ctypes.c_void_p)))
+    return tickets
+
+
+def fks_server_wait(s: Server, ticket: int):
+    st, lat = ctypes.c_int(), ctypes.c_double()
+    _check(_server_lib().fks_server_wait(s.handle, ticket, ctypes.byref(st), ctypes.byref(lat)))
+    return st.value, lat.value
+
+
+def fks_server_drain(s: Server):
+    _check(_server_lib().fks_server_drain(s.handle))
+
+
+def fks_server_stats(s: Server) -> fks_server_stats_t:
+    o = fks_server_stats_t()
+    _check(_server_lib().fks_server_stats(s.handle, ctypes.byref(o)))
+    return o
+
+
+def fks_server_map(s: Server, map_id: int):
+    h = _server_lib().fks_server_map(s.handle, map_id)
+    return Map(h, owner=s) if h else None
+
+
 def fks_status_str(status: int) -> str:
     return lib().fks_status_str(status).decode()
 

@@ -292,3 +292,258 @@ def batched_workload(m: int, n_lo: int, n_hi: int, nq: int, hit_frac: float, see
     q[~hit] = cand
     ev = np.where(hit, li, -1).astype(np.int64)
     return BatchedWorkload(keys, vals, seg, build_seeds, key_seeds, q_map, q, hit.astype(np.uint8), ev)
+
+
+# ----------------------------------------------------------------------- serving
+U64_MAP_BYTES_PER_KEY = 72     # descriptor 8 B + slot capacity 4 x 16 B
+STR_MAP_BYTES_PER_KEY = 136    # descriptor 8 B + slot capacity 4 x 32 B (+ context bytes)
+
+
+@dataclass
+class ServePlan:
+    """A request stream: kind 0 = build, 1 = lookup; key_kind 0 = uint64,
+    1 = strings.  Builds take map ids 0, 1, ... in order; a map's keys are
+    the pool entries [off, off + n).  A lookup of nq needles has nhit members
+    of its target map, the rest non-members.  The first `prefill` requests
+    are builds."""
+    kind: np.ndarray
+    key_kind: np.ndarray
+    map_id: np.ndarray
+    n: np.ndarray
+    off: np.ndarray
+    seed: np.ndarray
+    nq: np.ndarray
+    nhit: np.ndarray
+    prefill: int
+    budget: int
+
+
+def serving_plan(n_requests: int, seed: int, budget: int, str_offs: np.ndarray, prefill: int = 64,
+                 lookup_frac: float = 0.9, hit_frac: float = 0.8, u64_n=(2**10, 2**22),
+                 str_n=(2**10, 2**20), nq_range=(1, 2**16), u64_pool: int = 2**22) -> ServePlan:
+    """prefill builds, then n_requests requests; lookups target a map drawn
+    uniformly from the maps resident at that point, under an LRU model of a
+    budget of `budget` bytes (the server's accounted map sizes), so every
+    lookup targets a map the server holds."""
+    import collections
+    rng = np.random.Generator(np.random.PCG64(seed))
+    str_pool = str_offs.size - 1
+    total = prefill + n_requests
+    kind = np.zeros(total, np.uint8)
+    key_kind = np.zeros(total, np.uint8)
+    map_id = np.zeros(total, np.uint32)
+    n = np.zeros(total, np.int64)
+    off = np.zeros(total, np.int64)
+    sd = np.zeros(total, np.uint64)
+    nq = np.zeros(total, np.int64)
+    nhit = np.zeros(total, np.int64)
+    resident = collections.OrderedDict()   # map id -> bytes, least recent first
+    ids, where = [], {}                    # uniform choice among resident maps
+    used, next_id = 0, 0
+
+    def drop(mid):
+        i = where.pop(mid)
+        last = ids.pop()
+        if last != mid:
+            ids[i] = last
+            where[last] = i
+
+    info = {}
+    for r in range(total):
+        is_build = r < prefill or rng.random() >= lookup_frac or not ids
+        if is_build:
+            kk = int(rng.random() < 0.5)
+            lo, hi = (str_n if kk else u64_n)
+            nn = int(np.floor(np.exp(rng.uniform(np.log(lo), np.log(hi)))))
+            pool = str_pool if kk else u64_pool
+            o = int(rng.integers(0, pool - nn + 1))
+            need = (STR_MAP_BYTES_PER_KEY * nn + int(str_offs[o + nn] - str_offs[o])) if kk \
+                else U64_MAP_BYTES_PER_KEY * nn
+            while used + need > budget and resident:
+                victim, b = resident.popitem(last=False)
+                used -= b
+                drop(victim)
+            mid = next_id
+            next_id += 1
+            resident[mid] = need
+            used += need
+            where[mid] = len(ids)
+            ids.append(mid)
+            info[mid] = (kk, nn, o)
+            kind[r], key_kind[r], map_id[r], n[r], off[r] = 0, kk, mid, nn, o
+            sd[r] = np.uint64(rng.integers(0, 2**63))
+        else:
+            mid = ids[int(rng.integers(0, len(ids)))]
+            resident.move_to_end(mid)
+            kk, nn, o = info[mid]
+            q = int(np.floor(np.exp(rng.uniform(np.log(nq_range[0]), np.log(nq_range[1])))))
+            kind[r], key_kind[r], map_id[r], n[r], off[r] = 1, kk, mid, nn, o
+            nq[r] = q
+            nhit[r] = rng.binomial(q, hit_frac)
+    return ServePlan(kind, key_kind, map_id, n, off, sd, nq, nhit, prefill, budget)
+
+
+def poisson_arrivals_us(count: int, rate_per_s: float, seed: int) -> np.ndarray:
+    """Arrival times (microseconds from the start) of a Poisson process."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return np.cumsum(rng.exponential(1e6 / rate_per_s, count))
+
+
+class ServeData:
+    """Device payloads of a ServePlan (torch tensors kept alive here) and the
+    request descriptors of the C ABI.  Map keys are slices of shared pools:
+    uint64 keys of the splitmix stream, strings of a string workload; lookup
+    needles are gathered on the device: members drawn uniformly (with
+    replacement) from the target map's slice, non-members from pools of
+    non-members of every map.  Values of a map are the index of the key in
+    the map's slice."""
+
+    def __init__(self, plan: ServePlan, seed: int, u64_pool: int = 2**22, strings=None):
+        import torch
+
+        from . import fks as F
+        dev = torch.device("cuda")
+        self.plan = plan
+        g = torch.Generator(device=dev)
+        g.manual_seed(seed)
+        pool = key_stream(seed, u64_pool)
+        self.u64_keys = torch.from_numpy(pool.view(np.int64)).to(dev)
+        self.u64_vals = torch.arange(u64_pool, dtype=torch.int64, device=dev)
+        miss = _non_members(seed, u64_pool, u64_pool)
+        self.u64_miss = torch.from_numpy(miss.view(np.int64)).to(dev)
+        s = strings
+        self.s_ctx = torch.from_numpy(s.ctx).to(dev)
+        self.s_offs_h = s.offs
+        self.s_offs = torch.from_numpy(s.offs).to(dev)
+        self.s_vals = torch.arange(s.offs.size - 1, dtype=torch.int64, device=dev)
+        self.m_ctx = torch.from_numpy(s.qctx).to(dev)     # non-member strings
+        self.m_offs = torch.from_numpy(s.qoffs).to(dev)
+        P = plan
+        builds = np.nonzero(P.kind == 0)[0]
+        looks = np.nonzero(P.kind == 1)[0]
+        # per-build relative offsets of string maps, one tensor
+        sb = builds[P.key_kind[builds] == 1]
+        rel_len = (P.n[sb] + 1).astype(np.int64)
+        rel_start = np.concatenate([[0], np.cumsum(rel_len)[:-1]]) if sb.size else np.zeros(0, np.int64)
+        self.rel_offs = torch.empty(int(rel_len.sum()), dtype=torch.int64, device=dev)
+        for k, r in enumerate(sb):
+            o, nn = int(P.off[r]), int(P.n[r])
+            self.rel_offs[rel_start[k]:rel_start[k] + nn + 1] = self.s_offs[o:o + nn + 1] - self.s_offs[o]
+        # uint64 needles of all uint64 lookups, gathered at once
+        ul = looks[P.key_kind[looks] == 0]
+        self.u_q, self.u_start, self.u_hit = self._gather_u64(P, ul, g, dev)
+        # string needles of all string lookups: one CSR over every request
+        sl = looks[P.key_kind[looks] == 1]
+        self.s_qctx, self.s_qoffs, self.s_start, self.s_hit, self.s_idx = self._gather_str(P, sl, g, dev)
+        nq_total = int(P.nq[looks].sum()) if looks.size else 0
+        self.out = torch.empty(max(nq_total, 1), dtype=torch.int64, device=dev)
+        self.found = torch.empty(max(nq_total, 1), dtype=torch.uint8, device=dev)
+        out_start = np.zeros(P.kind.size, np.int64)
+        if looks.size:
+            out_start[looks] = np.concatenate([[0], np.cumsum(P.nq[looks])[:-1]])
+        self.out_start = out_start
+        # request descriptors
+        reqs = (F.fks_request * P.kind.size)()
+        ub = {int(r): k for k, r in enumerate(sb)}
+        u_index = {int(r): k for k, r in enumerate(ul)}
+        s_index = {int(r): k for k, r in enumerate(sl)}
+        for r in range(P.kind.size):
+            q = reqs[r]
+            q.struct_size = ctypes_sizeof_request()
+            q.map_id = int(P.map_id[r])
+            q.key_kind = int(P.key_kind[r])
+            o, nn = int(P.off[r]), int(P.n[r])
+            if P.kind[r] == 0:
+                q.type = F.FKS_REQ_BUILD
+                q.n = nn
+                q.seed = int(P.seed[r])
+                if P.key_kind[r] == 0:
+                    q.val_type = F.FKS_VAL_I64
+                    q.keys = self.u64_keys.data_ptr() + 8 * o
+                    q.vals = self.u64_vals.data_ptr()
+                else:
+                    q.val_type = F.FKS_VAL_I64
+                    base = int(self.s_offs_h[o])
+                    q.ctx = self.s_ctx.data_ptr() + base
+                    q.ctx_bytes = int(self.s_offs_h[o + nn]) - base
+                    q.offs = self.rel_offs.data_ptr() + 8 * int(rel_start[ub[r]])
+                    q.vals = self.s_vals.data_ptr()
+            else:
+                q.type = F.FKS_REQ_LOOKUP
+                q.nq = int(P.nq[r])
+                q.absent = -1
+                q.out_vals = self.out.data_ptr() + 8 * int(out_start[r])
+                q.out_found = self.found.data_ptr() + int(out_start[r])
+                if P.key_kind[r] == 0:
+                    q.q = self.u_q.data_ptr() + 8 * int(self.u_start[u_index[r]])
+                else:
+                    q.qctx = self.s_qctx.data_ptr()
+                    q.qoffs = self.s_qoffs.data_ptr() + 8 * int(self.s_start[s_index[r]])
+        self.reqs = reqs
+        self.u_index, self.s_index = u_index, s_index
+
+    def _gather_u64(self, P, rows, g, dev):
+        import torch
+        if rows.size == 0:
+            z = torch.zeros(1, dtype=torch.int64, device=dev)
+            return z, np.zeros(0, np.int64), torch.zeros(1, dtype=torch.bool, device=dev)
+        nq = torch.from_numpy(P.nq[rows]).to(dev)
+        req = torch.repeat_interleave(torch.arange(rows.size, device=dev), nq)
+        start = torch.cumsum(nq, 0) - nq
+        pos = torch.arange(req.numel(), device=dev) - start[req]
+        hit = pos < torch.from_numpy(P.nhit[rows]).to(dev)[req]
+        rnd = torch.randint(0, 2**62, (req.numel(),), device=dev, generator=g)
+        n = torch.from_numpy(P.n[rows]).to(dev)[req]
+        off = torch.from_numpy(P.off[rows]).to(dev)[req]
+        hidx = off + rnd % n
+        midx = rnd % self.u64_miss.numel()
+        q = torch.where(hit, self.u64_keys[hidx], self.u64_miss[midx])
+        self.u_expect = torch.where(hit, hidx - off, torch.full_like(hidx, -1))
+        return q, start.cpu().numpy(), hit
+
+    def _gather_str(self, P, rows, g, dev):
+        import torch
+        if rows.size == 0:
+            z = torch.zeros(2, dtype=torch.int64, device=dev)
+            return torch.zeros(1, dtype=torch.uint8, device=dev), z, np.zeros(0, np.int64), \
+                torch.zeros(1, dtype=torch.bool, device=dev), z
+        nq = torch.from_numpy(P.nq[rows]).to(dev)
+        req = torch.repeat_interleave(torch.arange(rows.size, device=dev), nq)
+        start = torch.cumsum(nq, 0) - nq
+        pos = torch.arange(req.numel(), device=dev) - start[req]
+        hit = pos < torch.from_numpy(P.nhit[rows]).to(dev)[req]
+        rnd = torch.randint(0, 2**62, (req.numel(),), device=dev, generator=g)
+        n = torch.from_numpy(P.n[rows]).to(dev)[req]
+        off = torch.from_numpy(P.off[rows]).to(dev)[req]
+        hidx = off + rnd % n
+        midx = rnd % (self.m_offs.numel() - 1)
+        idx = torch.where(hit, hidx, midx)
+        src_start = torch.where(hit, self.s_offs[idx], self.m_offs[idx])
+        lens = torch.where(hit, self.s_offs[idx + 1] - self.s_offs[idx], self.m_offs[idx + 1] - self.m_offs[idx])
+        qoffs = torch.zeros(idx.numel() + 1, dtype=torch.int64, device=dev)
+        qoffs[1:] = torch.cumsum(lens, 0)
+        qctx = torch.empty(int(qoffs[-1]), dtype=torch.uint8, device=dev)
+        self.s_expect = torch.where(hit, hidx - off, torch.full_like(hidx, -1))
+        # gather the bytes in chunks of strings (bounded index tensors)
+        chunk = 1 << 22
+        for a in range(0, idx.numel(), chunk):
+            b = min(idx.numel(), a + chunk)
+            ln = lens[a:b]
+            dst0 = qoffs[a:b]
+            which = torch.repeat_interleave(torch.arange(b - a, device=dev), ln)
+            within = torch.arange(which.numel(), device=dev) - (dst0 - qoffs[a])[which]
+            srcpos = src_start[a:b][which] + within
+            h = hit[a:b][which]
+            bytes_ = torch.where(h, self.s_ctx[srcpos.clamp(max=self.s_ctx.numel() - 1)],
+                                 self.m_ctx[srcpos.clamp(max=self.m_ctx.numel() - 1)])
+            qctx[int(qoffs[a]):int(qoffs[b])] = bytes_
+        # per-request CSR slices share one offsets array: a request starting at
+        # string s uses qoffs[s .. s + nq] (absolute offsets into qctx)
+        return qctx, qoffs, start.cpu().numpy(), hit, idx
+
+
+def ctypes_sizeof_request() -> int:
+    import ctypes
+
+    from . import fks as F
+    return ctypes.sizeof(F.fks_request)
