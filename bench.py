@@ -282,6 +282,9 @@ def run_serving(args, F, W, torch):
     arrival = W.poisson_arrivals_us(m, args.serve_rho * mu, 5)
     out["per_call"] = once(F.FKS_SERVE_PER_CALL, arrival)
     out["batched"] = once(F.FKS_SERVE_BATCHED, arrival)
+    over = W.poisson_arrivals_us(m, 1.2 * mu, 6)
+    out["over_saturation_rho_1_2"] = {"per_call": once(F.FKS_SERVE_PER_CALL, over),
+                                      "batched": once(F.FKS_SERVE_BATCHED, over)}
     # the batched run's results against the stream's truth
     f = data.found.cpu().numpy()
     looks = np.nonzero(plan.kind == 1)[0]

@@ -59,6 +59,7 @@ struct MapSlot {
   uint64_t lru = 0;
   uint32_t inflight = 0;       // lookups routed to the map and not yet complete
   bool free_when_idle = false; // evicted while lookups were in flight
+  bool discard = false;        // evicted while its build was running
   std::vector<Req*> parked;    // lookups waiting for the map's build
   LookupMap view{};
   int strings = 0, out_i64 = 1;
@@ -86,7 +87,7 @@ struct fks_server {
   std::atomic<bool> stop{false};
   // scheduler state
   std::vector<MapSlot> maps;
-  std::set<std::pair<uint64_t, uint32_t>> lru;  // (last use, id) of ready maps
+  std::set<std::pair<uint64_t, uint32_t>> lru;  // (last use, id) of resident maps (ready or building)
   uint64_t used = 0, peak = 0, seq = 0;
   uint64_t evictions = 0, rejected = 0, batches = 0;
   std::vector<Req*> ready;       // lookups ready for the next batch
@@ -116,9 +117,10 @@ void complete(fks_server* S, Req* q, fks_status st) {
 
 void touch(fks_server* S, uint32_t id) {
   MapSlot& m = S->maps[id];
-  if (m.state == kReady) S->lru.erase({m.lru, id});
+  const bool resident = m.state == kReady || m.state == kBuilding;
+  if (resident) S->lru.erase({m.lru, id});
   m.lru = ++S->seq;
-  if (m.state == kReady) S->lru.insert({m.lru, id});
+  if (resident) S->lru.insert({m.lru, id});
 }
 
 void release_map(fks_server* S, uint32_t id) {
@@ -130,7 +132,9 @@ void release_map(fks_server* S, uint32_t id) {
   (void)S;
 }
 
-// Evict least-recently-used ready maps until `need` more bytes fit.
+// Evict least-recently-used resident maps until `need` more bytes fit.  A
+// map still being built is evicted all the same (residency follows arrival
+// order exactly); its result is discarded when the build finishes.
 bool admit(fks_server* S, uint64_t need) {
   while (S->used + need > S->opts.memory_budget && !S->lru.empty()) {
     const uint32_t id = S->lru.begin()->second;
@@ -138,8 +142,13 @@ bool admit(fks_server* S, uint64_t need) {
     MapSlot& m = S->maps[id];
     S->used -= m.bytes;
     m.bytes = 0;
-    m.state = kEvicted;
     ++S->evictions;
+    if (m.state == kBuilding) {
+      m.discard = true;
+      m.state = kEvicted;
+      continue;
+    }
+    m.state = kEvicted;
     if (m.inflight == 0) release_map(S, id);
     else m.free_when_idle = true;  // freed once its in-flight lookups finish
   }
@@ -204,7 +213,7 @@ void apply_arrival(fks_server* S, Req* q) {
     return;
   }
   MapSlot& m = S->maps[r.map_id];
-  if (m.state == kReady || m.state == kBuilding || m.free_when_idle) {  // the id is taken
+  if (m.state == kReady || m.state == kBuilding || m.free_when_idle || m.discard) {  // the id is taken
     complete(S, q, FKS_ERR_INVALID_ARG);
     return;
   }
@@ -220,6 +229,7 @@ void apply_arrival(fks_server* S, Req* q) {
   m.bytes = need;
   m.map = nullptr;
   m.lru = ++S->seq;
+  S->lru.insert({m.lru, r.map_id});
   {
     std::lock_guard<std::mutex> lk(S->bmu);
     S->build_queue.push_back(q);
@@ -231,17 +241,22 @@ void apply_build_result(fks_server* S, Req* q) {
   MapSlot& m = S->maps[q->r.map_id];
   std::vector<Req*> parked;
   parked.swap(m.parked);
-  if (q->status == FKS_OK) {
+  if (m.discard) {  // evicted while building: drop the result
+    if (q->built) fks_map_destroy(q->built);
+    m.discard = false;
+    for (Req* l : parked) {
+      --m.inflight;
+      complete(S, l, FKS_ERR_EVICTED);
+    }
+  } else if (q->status == FKS_OK) {
     m.map = q->built;
     m.state = kReady;
     fks::lookup_view_of(m.map, &m.view, &m.strings, &m.out_i64);
-    S->lru.insert({m.lru, q->r.map_id});
     for (Req* l : parked) S->ready.push_back(l);
   } else {
-    if (m.state == kBuilding) {
-      S->used -= m.bytes;
-      m.bytes = 0;
-    }
+    S->lru.erase({m.lru, q->r.map_id});
+    S->used -= m.bytes;
+    m.bytes = 0;
     m.state = kEmpty;
     for (Req* l : parked) {
       lookup_done(S, l);
