@@ -241,12 +241,21 @@ void apply_build_result(fks_server* S, Req* q) {
   MapSlot& m = S->maps[q->r.map_id];
   std::vector<Req*> parked;
   parked.swap(m.parked);
-  if (m.discard) {  // evicted while building: drop the result
-    if (q->built) fks_map_destroy(q->built);
+  if (m.discard) {
+    // Evicted while building.  Lookups that arrived before the eviction are
+    // still served; the map is freed once they finish.
     m.discard = false;
-    for (Req* l : parked) {
-      --m.inflight;
-      complete(S, l, FKS_ERR_EVICTED);
+    if (q->status == FKS_OK && !parked.empty()) {
+      m.map = q->built;
+      fks::lookup_view_of(m.map, &m.view, &m.strings, &m.out_i64);
+      m.free_when_idle = true;
+      for (Req* l : parked) S->ready.push_back(l);
+    } else {
+      if (q->built) fks_map_destroy(q->built);
+      for (Req* l : parked) {
+        --m.inflight;
+        complete(S, l, q->status == FKS_OK ? FKS_ERR_EVICTED : q->status);
+      }
     }
   } else if (q->status == FKS_OK) {
     m.map = q->built;

@@ -87,7 +87,7 @@ def test_a_served_lookup_equals_the_same_lookup_alone(F, strings):
         m = F.fks_server_map(srv, int(P.map_id[r]))
         assert m is not None
         nq = int(P.nq[r])
-        out = torch.empty(nq, dtype=torch.int64 if P.key_kind[r] == 0 else torch.int32, device="cuda")
+        out = torch.empty(nq, dtype=torch.int64, device="cuda")
         found = torch.empty(nq, dtype=torch.uint8, device="cuda")
         import ctypes
         if P.key_kind[r] == 0:
