@@ -233,6 +233,76 @@ def run_reference(args, world, rank):
     print(json.dumps(line))
 
 
+def _timed(torch, stream, fn, reps=3, warm=1):
+    ts = []
+    for i in range(warm + reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        if i >= warm:
+            ts.append(a.elapsed_time(b))
+        del r
+    return statistics.median(ts)
+
+
+def run_strings(F, W, torch, hbm):
+    """Config 3: 2^22 distinct strings (lengths uniform in [4, 64], a-z) with
+    int32 values; 2^24 needles, 50 % members."""
+    w = W.string_workload(1 << 22, 1 << 24, 0.5, seed=3)
+    ctx, offs = torch.from_numpy(w.ctx).cuda(), torch.from_numpy(w.offs).cuda()
+    vals = torch.from_numpy(w.vals.astype(np.int32)).cuda()
+    qctx, qoffs = torch.from_numpy(w.qctx).cuda(), torch.from_numpy(w.qoffs).cuda()
+    nq = w.qoffs.size - 1
+    out = torch.empty(nq, dtype=torch.int32, device="cuda")
+    found = torch.empty(nq, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    bms = _timed(torch, stream, lambda: F.fks_build_bytes(ctx, offs, vals, 3))
+    m = F.fks_build_bytes(ctx, offs, vals, 3)
+    lms = _timed(torch, stream, lambda: F.fks_lookup_bytes(m, qctx, qoffs, out, found, -1))
+    ok = np.array_equal(found.cpu().numpy(), w.expect_found)
+    info = F.fks_map_info(m)
+    L = float(np.diff(w.offs).mean())
+    Lq = float(np.diff(w.qoffs).mean())
+    ne = info.nonempty_buckets / info.n
+    # needle: offsets 8 + bytes + descriptor sector + slot sector (hits, misses in
+    # non-empty buckets) + on a hit the map's context span (1 + (L-1)/32 sectors)
+    # + value 4 + found 1
+    lq = 8 + Lq + 32 + 32 * (0.5 + 0.5 * ne) + 0.5 * 32 * (1 + (L - 1) / 32) + 4 + 1
+    n = w.offs.size - 1
+    return {"workload": "2^22 strings (4..64 bytes, a-z), int32 values; 2^24 needles, 50% members",
+            "build_ms": bms, "build_keys_per_s": n / (bms / 1e3), "lookup_ms": lms,
+            "lookups_per_s": nq / (lms / 1e3), "lookup_bytes_model": f"{lq:.1f} B/needle",
+            "lookup_GBps": lq * nq / (lms / 1e3) / 1e9, "lookup_frac": lq * nq / (lms / 1e3) / 1e9 / hbm,
+            "results_match_truth": bool(ok), "S_over_n": info.slots / info.n}
+
+
+def run_batched(F, W, torch, hbm):
+    """Config 4: 1024 maps of log-uniform size in [16, 2^20] built by one
+    batched call; 2^24 (map_id, key) lookups at 75 % hits."""
+    b = W.batched_workload(1024, 16, 1 << 20, 1 << 24, 0.75, seed=4)
+    keys = torch.from_numpy(b.keys.view(np.int64)).cuda()
+    vals = torch.from_numpy(b.vals).cuda()
+    ids = torch.from_numpy(b.q_map.astype(np.int32)).cuda()
+    q = torch.from_numpy(b.q_keys.view(np.int64)).cuda()
+    out = torch.empty(q.numel(), dtype=torch.int64, device="cuda")
+    found = torch.empty(q.numel(), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    total = int(b.seg_offs[-1])
+    bms = _timed(torch, stream, lambda: F.fks_build_batched(F.FKS_KEY_U64, keys, None, None, b.seg_offs, b.seeds,
+                                                              vals))
+    S = F.fks_build_batched(F.FKS_KEY_U64, keys, None, None, b.seg_offs, b.seeds, vals)
+    lms = _timed(torch, stream, lambda: F.fks_lookup_batched(S, ids, q=q, out_vals=out, out_found=found))
+    ok = np.array_equal(found.cpu().numpy(), b.expect_found)
+    lq = 4 + 8 + 32 + 32 * (0.75 + 0.25 * 0.632) + 8 + 1
+    return {"workload": "1024 maps, n log-uniform in [16, 2^20] (sum %d keys); 2^24 lookups, 75%% hits" % total,
+            "build_ms": bms, "build_keys_per_s": total / (bms / 1e3), "lookup_ms": lms,
+            "lookups_per_s": q.numel() / (lms / 1e3), "lookup_bytes_model": f"{lq:.1f} B/query",
+            "lookup_GBps": lq * q.numel() / (lms / 1e3) / 1e9,
+            "lookup_frac": lq * q.numel() / (lms / 1e3) / 1e9 / hbm, "results_match_truth": bool(ok)}
+
+
 def run_serving(args, F, W, torch):
     """Config 5: a Poisson stream of build and lookup requests (90 % lookups of
     log-uniform size in [1, 2^16], 80 % hits; 10 % builds, half uint64 maps of
@@ -310,6 +380,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-search-baseline", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=20000)
+    ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--serve-rho", type=float, default=0.8)
     ap.add_argument("--n", type=int, default=N_KEYS)
     args = ap.parse_args()
@@ -516,6 +587,10 @@ def main():
             "build_ms": med(sb), "lookup_ms": med(sl),
             "build_keys_per_s": n / (med(sb) / 1e3), "lookups_per_s": nq / (med(sl) / 1e3),
             "fks_speedup_build": med(sb) / med(build_ms), "fks_speedup_lookup": med(sl) / lk}
+    # ---- the other rows of the path: string keys (config 3), batched maps (config 4)
+    if not args.no_extras:
+        line["strings"] = run_strings(F, W, torch, hbm)
+        line["batched"] = run_batched(F, W, torch, hbm)
     # ---- serving stream (config 5): continuous batching against per-call launches
     if args.serve_requests > 0:
         line["serving"] = run_serving(args, F, W, torch)

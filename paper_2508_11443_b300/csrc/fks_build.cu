@@ -514,12 +514,13 @@ __device__ __forceinline__ bool same_member(const PassDev& p, const uint64_t* gp
 
 enum { kSearchDup = -1, kSearchNext = -2 };
 
-// make_2 for one bucket by one thread: the first attempt whose s hashes
-// into s^2 slots are pairwise distinct.
+// make_2 for one bucket of 2 <= s <= 8 keys by one thread: the first attempt
+// whose s hashes into s^2 <= 64 slots are pairwise distinct; the slot
+// occupancy is a 64-bit register bitmap, returned with the constants.
 template <int PW>
 __device__ int search_thread(const PassDev& p, const uint64_t* k, const uint64_t* gpay,
                              uint32_t g0, uint32_t s, uint64_t seed, uint32_t round, uint32_t b,
-                             HashConsts* found) {
+                             HashConsts* found, uint64_t* occupied) {
   const uint32_t m = s * s;
   for (uint32_t a = 0; a < p.cfg.attempt_cap; ++a) {
     if (a == kDupCheckAttempt) {
@@ -535,23 +536,19 @@ __device__ int search_thread(const PassDev& p, const uint64_t* k, const uint64_t
     }
     const HashConsts c = derive(seed, round, b, a);
     bool col = false;
-    if (s <= 8) {
-      uint64_t bits = 0;
-      for (uint32_t x = 0; x < s; ++x) {
+    uint64_t bits = 0;
+#pragma unroll
+    for (uint32_t x = 0; x < kThreadSearchMax; ++x) {
+      if (x < s) {
         const uint64_t bit = 1ull << reduce32(hash32(c, k[x]), m);
         col |= (bits & bit) != 0;
         bits |= bit;
-      }
-    } else {
-      uint16_t js[kThreadSearchMax];
-      for (uint32_t x = 0; x < s; ++x) {
-        js[x] = uint16_t(reduce32(hash32(c, k[x]), m));
-        for (uint32_t y = 0; y < x; ++y) col |= js[y] == js[x];
       }
     }
     if (a < p.cfg.reject) continue;
     if (!col) {
       *found = c;
+      *occupied = bits;
       return int(a);
     }
   }
@@ -570,33 +567,78 @@ __device__ __forceinline__ void write_slot(const PassDev& p, uint64_t idx, uint6
   }
 }
 
-// Place one searched bucket (thread level).  owner mode: record member /
-// filler indices in the shared slot image; else write the slots directly.
+// Place one searched bucket (thread level, s <= 8).  owner mode: record
+// member / filler indices in the shared slot image; else write the slots
+// directly.  `bits` marks the occupied slots of the bucket's range.
 template <int PW>
 __device__ void place_thread(const PassDev& p, const uint64_t* k, const uint64_t* gpay,
-                             uint32_t g0, uint32_t s, const HashConsts& c, uint16_t* owner,
+                             uint32_t g0, uint32_t s, const HashConsts& c, uint64_t bits, uint16_t* owner,
                              uint32_t so, uint64_t slot0, bool owner_mode) {
   const uint32_t m = s * s;
-  uint32_t jmin = 0xFFFFFFFFu, xmin = 0;
+  const uint32_t jmin = uint32_t(__ffsll(static_cast<long long>(bits)) - 1);
+  uint32_t xmin = 0;
   for (uint32_t x = 0; x < s; ++x) {
     const uint32_t jj = reduce32(hash32(c, k[x]), m);
-    if (jj < jmin) {
-      jmin = jj;
-      xmin = x;
-    }
+    if (jj == jmin) xmin = x;
     if (owner_mode) owner[so + jj] = uint16_t(g0 + x);
+    else write_slot<PW>(p, slot0 + jj, k[x], gpay + PW * (g0 + x), false);
   }
-  if (owner_mode) {
-    for (uint32_t t = 0; t < m; ++t)
-      if (owner[so + t] == kOwnerEmpty) owner[so + t] = uint16_t(kOwnerFill | (g0 + xmin));
-  } else {
-    for (uint32_t t = 0; t < m; ++t) write_slot<PW>(p, slot0 + t, k[xmin], gpay + PW * (g0 + xmin), true);
-    for (uint32_t x = 0; x < s; ++x)
-      write_slot<PW>(p, slot0 + reduce32(hash32(c, k[x]), m), k[x], gpay + PW * (g0 + x), false);
+  // the rest of the range: the lowest occupied slot's key, value -1
+  uint64_t empty = ~bits & (m == 64 ? ~0ull : ((1ull << m) - 1));
+  while (empty) {
+    const uint32_t t = uint32_t(__ffsll(static_cast<long long>(empty)) - 1);
+    empty &= empty - 1;
+    if (owner_mode) owner[so + t] = uint16_t(kOwnerFill | (g0 + xmin));
+    else write_slot<PW>(p, slot0 + t, k[xmin], gpay + PW * (g0 + xmin), true);
   }
 }
 
-// make_2 + placement for a bucket larger than kThreadSearchMax, by the CTA.
+// make_2 + placement for a bucket of kThreadSearchMax < s <= 32 keys by one
+// warp: lane x holds key x, a collision is two lanes with the same slot
+// (__match_any_sync).  Returns the attempt (or kSearchDup / kSearchNext).
+template <int PW>
+__device__ int search_place_warp(const PassDev& p, const uint64_t* k, const uint64_t* gpay, uint32_t g0,
+                                 uint32_t s, uint64_t seed, uint32_t round, uint32_t b, uint16_t* owner,
+                                 uint32_t so, uint64_t slot0, bool owner_mode) {
+  const uint32_t lane = lane_id(), m = s * s;
+  const bool mine = lane < s;
+  const uint64_t key = mine ? k[lane] : 0;
+  for (uint32_t a = 0; a < p.cfg.attempt_cap; ++a) {
+    if (a == kDupCheckAttempt) {
+      const uint32_t same = __match_any_sync(0xFFFFFFFFu, mine ? key : ~0ull);
+      bool eq = false, dup = false;
+      if (mine && __popc(same) > 1) {
+        eq = true;
+        for (uint32_t lower = same & lanemask_lt(); lower; lower &= lower - 1)  // every pair, as the oracle
+          dup |= same_member<PW>(p, gpay, g0 + uint32_t(__ffs(lower) - 1), g0 + lane);
+      }
+      if (__any_sync(0xFFFFFFFFu, dup)) return kSearchDup;
+      if (__any_sync(0xFFFFFFFFu, eq)) return kSearchNext;
+    }
+    const HashConsts c = derive(seed, round, b, a);
+    const uint32_t jj = mine ? reduce32(hash32(c, key), m) : 0xFFFFFFFFu - lane;
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, jj);
+    const bool col = __any_sync(0xFFFFFFFFu, mine && __popc(peers) > 1);
+    if (a < p.cfg.reject || col) continue;
+    // place: members, then the filler in every other slot of the range
+    const uint32_t jmin = __reduce_min_sync(0xFFFFFFFFu, mine ? jj : 0xFFFFFFFFu);
+    const uint32_t xmin = __ffs(__ballot_sync(0xFFFFFFFFu, mine && jj == jmin)) - 1;
+    if (owner_mode) {
+      if (mine) owner[so + jj] = uint16_t(g0 + lane);
+      __syncwarp();
+      for (uint32_t t = lane; t < m; t += 32)
+        if (owner[so + t] == kOwnerEmpty) owner[so + t] = uint16_t(kOwnerFill | (g0 + xmin));
+    } else {
+      for (uint32_t t = lane; t < m; t += 32) write_slot<PW>(p, slot0 + t, k[xmin], gpay + PW * (g0 + xmin), true);
+      __syncwarp();
+      if (mine) write_slot<PW>(p, slot0 + jj, key, gpay + PW * (g0 + lane), false);
+    }
+    return int(a);
+  }
+  return kSearchNext;
+}
+
+// make_2 + placement for a bucket larger than kWarpSearchMax, by the CTA.
 template <int PW>
 __device__ __noinline__ void search_place_cta(const PassDev& p, const uint64_t* k, const uint64_t* gpay,
                                               uint32_t g0, uint32_t s, uint64_t seed, uint32_t round,
@@ -687,17 +729,28 @@ __device__ void search_partition(const PassDev& p, const MapRegs& M, uint32_t j,
                                  uint16_t* work, PartCtl& ctl) {
   // empty and single-key buckets need no search (attempt 0); the others are
   // compacted into a worklist so that searching lanes sit side by side
-  for (uint32_t lb = threadIdx.x; lb < nb; lb += kPartThreads) {
-    const uint32_t g0 = gst[lb], s = gst[lb + 1] - g0;
-    att[lb] = 0;
-    if (s == 1) {
-      if (owner_mode) owner[soff[lb]] = uint16_t(g0);
-      else write_slot<PW>(p, slot_part + soff[lb], gkey[g0], gpay + PW * g0, false);
-    } else if (s > 1 && s <= kThreadSearchMax) {
-      work[atomicAdd(&ctl.nwork, 1u)] = uint16_t(lb);
-    } else if (s > kThreadSearchMax) {
-      atomicAdd(&ctl.nbig, 1u);
+  // (one shared atomic per warp, not per bucket)
+  for (uint32_t lb0 = threadIdx.x & ~31u; lb0 < kB; lb0 += kPartThreads) {
+    const uint32_t lb = lb0 + lane_id();
+    uint32_t g0 = 0, s = 0;
+    if (lb < nb) {
+      g0 = gst[lb];
+      s = gst[lb + 1] - g0;
+      att[lb] = 0;
+      if (s == 1) {
+        if (owner_mode) owner[soff[lb]] = uint16_t(g0);
+        else write_slot<PW>(p, slot_part + soff[lb], gkey[g0], gpay + PW * g0, false);
+      }
     }
+    const bool want = lb < nb && s > 1 && s <= kThreadSearchMax;
+    const uint32_t m = __ballot_sync(0xFFFFFFFFu, want);
+    uint32_t base = 0;
+    if (lane_id() == 0 && m) base = atomicAdd(&ctl.nwork, uint32_t(__popc(m)));
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    if (want) work[base + __popc(m & lanemask_lt())] = uint16_t(lb);
+    // larger buckets go to the end of the worklist (warp or CTA searches)
+    const bool big = lb < nb && s > kThreadSearchMax;
+    if (big) work[kB - 1 - atomicAdd(&ctl.nbig, 1u)] = uint16_t(lb);
   }
   __syncthreads();
   uint32_t my_max = 0;
@@ -707,24 +760,59 @@ __device__ void search_partition(const PassDev& p, const MapRegs& M, uint32_t j,
     const uint32_t lb = work[w];
     const uint32_t g0 = gst[lb], s = gst[lb + 1] - g0;
     HashConsts c;
-    const int a = search_thread<PW>(p, gkey + g0, gpay, g0, s, M.seed, M.round, b0 + lb, &c);
+    uint64_t bits = 0;
+    const int a = search_thread<PW>(p, gkey + g0, gpay, g0, s, M.seed, M.round, b0 + lb, &c, &bits);
     if (a >= 0) {
       att[lb] = uint16_t(a);
       my_max = max(my_max, uint32_t(a));
       my_sum += uint64_t(a);
-      place_thread<PW>(p, gkey + g0, gpay, g0, s, c, owner, soff[lb], slot_part + soff[lb], owner_mode);
+      place_thread<PW>(p, gkey + g0, gpay, g0, s, c, bits, owner, soff[lb], slot_part + soff[lb], owner_mode);
     } else {
       atomicExch(a == kSearchDup ? &p.status[j].dup : &p.status[j].next_round, 1u);
       ctl.failed = 1;
     }
   }
-  if (my_max) atomicMax(&ctl.maxatt, my_max);
-  if (my_sum) atomicAdd(reinterpret_cast<unsigned long long*>(&ctl.attsum), my_sum);
+  // statistics: one shared atomic per warp
+  my_max = __reduce_max_sync(0xFFFFFFFFu, my_max);
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) my_sum += __shfl_xor_sync(0xFFFFFFFFu, my_sum, d);
+  if (lane_id() == 0) {
+    if (my_max) atomicMax(&ctl.maxatt, my_max);
+    if (my_sum) atomicAdd(reinterpret_cast<unsigned long long*>(&ctl.attsum), my_sum);
+  }
   __syncthreads();
   if (ctl.nbig) {
-    for (uint32_t lb = 0; lb < nb; ++lb) {  // uniform over the CTA
+    const uint32_t nbig = ctl.nbig;
+    // 8 < s <= 32: one warp per bucket
+    uint32_t wmax = 0;
+    uint64_t wsum = 0;
+    for (uint32_t i = threadIdx.x >> 5; i < nbig; i += kPartThreads / 32) {
+      const uint32_t lb = work[kB - 1 - i];
       const uint32_t g0 = gst[lb], s = gst[lb + 1] - g0;
-      if (s <= kThreadSearchMax) continue;
+      if (s > kWarpSearchMax) continue;
+      const int a = search_place_warp<PW>(p, gkey + g0, gpay, g0, s, M.seed, M.round, b0 + lb, owner, soff[lb],
+                                          slot_part + soff[lb], owner_mode);
+      if (lane_id() == 0) {
+        if (a >= 0) {
+          att[lb] = uint16_t(a);
+          wmax = max(wmax, uint32_t(a));
+          wsum += uint64_t(a);
+        } else {
+          atomicExch(a == kSearchDup ? &p.status[j].dup : &p.status[j].next_round, 1u);
+          ctl.failed = 1;
+        }
+      }
+    }
+    if (lane_id() == 0) {
+      if (wmax) atomicMax(&ctl.maxatt, wmax);
+      if (wsum) atomicAdd(reinterpret_cast<unsigned long long*>(&ctl.attsum), wsum);
+    }
+    __syncthreads();
+    // s > 32 (adversarial inputs only): the whole CTA, one bucket at a time
+    for (uint32_t i = 0; i < nbig; ++i) {
+      const uint32_t lb = work[kB - 1 - i];
+      const uint32_t g0 = gst[lb], s = gst[lb + 1] - g0;
+      if (s <= kWarpSearchMax) continue;
       search_place_cta<PW>(p, gkey + g0, gpay, g0, s, M.seed, M.round, b0 + lb, owner, soff[lb],
                            slot_part + soff[lb], owner_mode, j, ctl, att + lb);
     }
@@ -779,6 +867,10 @@ __global__ void __launch_bounds__(kPartThreads, PW == 1 ? 2 : 1) k_part_build(Pa
   uint16_t* att = reinterpret_cast<uint16_t*>(smem + L::kAtt);
   uint16_t* work = reinterpret_cast<uint16_t*>(smem + L::kWork);
   __shared__ PartCtl ctl;
+  // the current partition's map, out of registers; two copies so that the
+  // next partition's can be written while the previous write-out still reads
+  __shared__ MapRegs sM[2];
+  uint32_t iter = 0;
   __shared__ __align__(8) uint64_t bar;
   const uint32_t t = threadIdx.x;
   constexpr uint32_t kPerThread = kCap / kPartThreads;
@@ -795,9 +887,9 @@ __global__ void __launch_bounds__(kPartThreads, PW == 1 ? 2 : 1) k_part_build(Pa
     const uint32_t issued = ctl.next_issued;
     if (gp >= p.P || ctl.abort) break;
     const uint32_t j = p.m == 1 ? 0u : upper_seg(p.part_seg, p.m, gp);
-    const MapRegs M = load_map(p, j);
-    const uint32_t b0 = (gp - M.part_begin) << kLogB;
-    const uint32_t nb = min(kB, M.n - b0);
+    if (t == 32) sM[iter & 1] = load_map(p, j);  // visible after the barrier below
+    const MapRegs& M = sM[iter & 1];
+    ++iter;
     const uint64_t e0 = p.part_start[gp], e1 = p.part_start[gp + 1];
     const uint32_t ne = uint32_t(e1 - e0 < 0xFFFFFFFFull ? e1 - e0 : 0xFFFFFFFFull);
     for (uint32_t i = t; i < kB; i += kPartThreads) cnt[i] = 0;
@@ -820,6 +912,8 @@ __global__ void __launch_bounds__(kPartThreads, PW == 1 ? 2 : 1) k_part_build(Pa
       ctl.maxs = ctl.maxatt = ctl.nonempty = ctl.nbig = ctl.failed = ctl.nwork = 0;
       ctl.attsum = 0;
     }
+    const uint32_t b0 = (gp - M.part_begin) << kLogB;
+    const uint32_t nb = min(kB, M.n - b0);
     const bool overflow = ne > kCap;
     const uint32_t shift = uint32_t(e0 & 1ull);  // raw key index of element e0
     uint16_t lbr[kPerThread], rk[kPerThread];
@@ -868,7 +962,9 @@ __global__ void __launch_bounds__(kPartThreads, PW == 1 ? 2 : 1) k_part_build(Pa
     }
     __syncthreads();
     // raw* is free again: stage the next partition while this one is searched
-    if (t == 0) {
+    // (by the last warp, which rarely has search work: the worklist fills
+    // the low warps first)
+    if (t == kPartThreads - 32) {
       ctl.next_gp = atomicAdd(p.ticket, 1u);
       ctl.next_issued = issue_stage<PW>(p, ctl.next_gp, raw_key, raw_pay, &bar);
     }

@@ -18,7 +18,8 @@ constexpr uint32_t kB = 1u << kLogB;
 constexpr uint32_t kCap = 2048;        // keys of a partition held in shared memory
 constexpr uint32_t kOwnerCap = 4096;   // slots of a partition staged in shared memory
 constexpr int kPartThreads = 512;      // threads of a partition CTA
-constexpr uint32_t kThreadSearchMax = 64;  // larger buckets are searched by the whole CTA
+constexpr uint32_t kThreadSearchMax = 8;   // buckets up to this size: one thread each
+constexpr uint32_t kWarpSearchMax = 32;   // up to this size: one warp (lane = key); larger: the CTA
 constexpr uint16_t kOwnerEmpty = 0xFFFF;
 constexpr uint16_t kOwnerFill = 0x8000;
 

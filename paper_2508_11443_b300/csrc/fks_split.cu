@@ -26,7 +26,7 @@ namespace {
 
 constexpr uint32_t kTile = 4096;     // keys per tile
 constexpr int kSplitThreads = 512;
-constexpr uint32_t kMaxBins = 2048;  // bins of one level
+constexpr uint32_t kMaxBins = 1024;  // bins of one level (larger shapes use the one-level path)
 constexpr uint32_t kScanItems = 8192;  // elements per block of the device-wide scan
 constexpr int kScanThreads = 512;
 
@@ -123,16 +123,19 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_scatterA(PassDev p, SplitD
   uint64_t* skey = reinterpret_cast<uint64_t*>(smem);
   uint64_t* spay = skey + kTile;
   uint32_t* sgp = reinterpret_cast<uint32_t*>(spay + PW * kTile);
-  __shared__ uint32_t cur[kMaxBins], lstart[kMaxBins], wsum[kSplitThreads / 32];
+  __shared__ uint32_t cur[kMaxBins], lstart[kMaxBins], dbase[kMaxBins], wsum[kSplitThreads / 32];
   __shared__ uint64_t sh_seg[2049];
   const uint64_t* seg = p.pass_seg;
   if (p.m > 1 && p.m <= 2048) {
     for (uint32_t i = threadIdx.x; i <= p.m; i += blockDim.x) sh_seg[i] = p.pass_seg[i];
     seg = sh_seg;
   }
-  for (uint32_t i = threadIdx.x; i < s.binsA; i += blockDim.x) cur[i] = 0;
-  __syncthreads();
   const uint32_t tile = blockIdx.x;
+  for (uint32_t i = threadIdx.x; i < s.binsA; i += blockDim.x) {
+    cur[i] = 0;
+    dbase[i] = s.histA[uint64_t(i) * s.tilesA + tile];  // this tile's output start per bin
+  }
+  __syncthreads();
   const uint64_t e0 = uint64_t(tile) * kTile, e1 = min(p.total, e0 + kTile);
   const uint32_t cnt = uint32_t(e1 - e0);
   constexpr uint32_t kPer = kTile / kSplitThreads;
@@ -189,7 +192,7 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_scatterA(PassDev p, SplitD
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
     const uint32_t gp = sgp[i], a = gp >> s.shiftB;
-    const uint64_t dst = uint64_t(s.histA[uint64_t(a) * s.tilesA + tile]) + (i - lstart[a]);
+    const uint64_t dst = uint64_t(dbase[a]) + (i - lstart[a]);
     s.keyA[dst] = skey[i];
     s.payA[PW * dst] = spay[PW * i];
     if (kStr) s.payA[PW * dst + 1] = spay[PW * i + 1];
@@ -253,12 +256,15 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_scatterB(PassDev p, SplitD
   uint64_t* skey = reinterpret_cast<uint64_t*>(smem);
   uint64_t* spay = skey + kTile;
   uint16_t* sdig = reinterpret_cast<uint16_t*>(spay + PW * kTile);
-  __shared__ uint32_t cur[kMaxBins], lstart[kMaxBins], wsum[kSplitThreads / 32];
+  __shared__ uint32_t cur[kMaxBins], lstart[kMaxBins], dbase[kMaxBins], wsum[kSplitThreads / 32];
   const uint32_t t = blockIdx.x;
   uint32_t a;
   uint64_t e0, e1;
   if (!tile_b(s, s.tstartB, t, &a, &e0, &e1)) return;
-  for (uint32_t i = threadIdx.x; i < s.binsB; i += blockDim.x) cur[i] = 0;
+  for (uint32_t i = threadIdx.x; i < s.binsB; i += blockDim.x) {
+    cur[i] = 0;
+    dbase[i] = s.histB[histB_index(s, s.tstartB, a, i, t)];  // this tile's output start per bin
+  }
   __syncthreads();
   const uint32_t cnt = uint32_t(e1 - e0), mask = s.binsB - 1;
   constexpr uint32_t kPer = kTile / kSplitThreads;
@@ -318,7 +324,7 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_scatterB(PassDev p, SplitD
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < cnt; i += blockDim.x) {
     const uint32_t dg = sdig[i];
-    const uint64_t dst = uint64_t(s.histB[histB_index(s, s.tstartB, a, dg, t)]) + (i - lstart[dg]);
+    const uint64_t dst = uint64_t(dbase[dg]) + (i - lstart[dg]);
     p.stage_key[dst] = skey[i];
     p.stage_pay[PW * dst] = spay[PW * i];
     if (kStr) p.stage_pay[PW * dst + 1] = spay[PW * i + 1];
