@@ -41,12 +41,14 @@ class _Info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint64), ("seed", ctypes.c_uint64), ("round", ctypes.c_uint32),
                 ("max_s", ctypes.c_uint32), ("S", ctypes.c_uint64), ("c1", ctypes.c_uint64 * 3),
                 ("attempts_sum", ctypes.c_uint64), ("nonempty", ctypes.c_uint64),
-                ("rounds_used", ctypes.c_uint32), ("max_attempt", ctypes.c_uint32)]
+                ("rounds_used", ctypes.c_uint32), ("max_attempt", ctypes.c_uint32),
+                ("nb", ctypes.c_uint64)]
 
 
 class _Opts(ctypes.Structure):
     _fields_ = [("bound_factor", ctypes.c_uint32), ("round_cap", ctypes.c_uint32),
-                ("attempt_cap", ctypes.c_uint32), ("reject_attempts", ctypes.c_uint32)]
+                ("attempt_cap", ctypes.c_uint32), ("reject_attempts", ctypes.c_uint32),
+                ("keys_per_bucket", ctypes.c_uint32)]
 
 
 def lib():
@@ -76,7 +78,7 @@ def lib():
         L.or_lookup_bytes.restype = None
         L.or_lookup_bytes.argtypes = [vp, vp, vp, u64, u64, u32, vp, vp, u64, ctypes.c_int64, vp, vp]
         L.or_l1_counts.restype = None
-        L.or_l1_counts.argtypes = [vp, u64, u64, u32, vp]
+        L.or_l1_counts.argtypes = [vp, u64, u64, u64, u32, vp]
         L.or_fingerprints.restype = None
         L.or_fingerprints.argtypes = [vp, vp, u64, u64, u32, vp]
         L.or_binary_search.restype = ctypes.c_int64
@@ -141,18 +143,31 @@ class Map:
     nonempty: int = 0
     rounds_used: int = 0
     max_attempt: int = 0
-    desc: np.ndarray | None = None      # uint64[n]
+    nb: int = 0                         # level-one buckets
+    keys_per_bucket: int = 1
+    desc: np.ndarray | None = None      # uint64[nb]
     slots: np.ndarray | None = None     # uint64[S, words]
     ctx: np.ndarray | None = None       # strings: the map's own context
     kind: str = "u64"
 
 
-def _opts(bound_factor=4, round_cap=32, attempt_cap=4095, reject_attempts=0):
-    return _Opts(bound_factor, round_cap, attempt_cap, reject_attempts)
+def buckets(n: int, keys_per_bucket: int = 1) -> int:
+    """Level-one buckets of an n-key map: ceil(n / keys_per_bucket)."""
+    return -(-n // keys_per_bucket)
 
 
-def _finish(st, info, n, seed, desc, slots, words, kind, ctx=None) -> Map:
-    m = Map(status=st, n=n, seed=seed, kind=kind)
+def default_bound(keys_per_bucket: int = 1) -> int:
+    return 2 * (1 + keys_per_bucket)
+
+
+def _opts(bound_factor=0, round_cap=32, attempt_cap=4095, reject_attempts=0, keys_per_bucket=1):
+    return _Opts(bound_factor or default_bound(keys_per_bucket), round_cap, attempt_cap,
+                 reject_attempts, keys_per_bucket)
+
+
+def _finish(st, info, n, seed, desc, slots, words, kind, ctx=None, lam=1) -> Map:
+    m = Map(status=st, n=n, seed=seed, kind=kind, nb=buckets(n, lam) if n else 0,
+            keys_per_bucket=lam)
     if st == OK:
         m.round, m.S, m.max_s = int(info.round), int(info.S), int(info.max_s)
         m.c1 = tuple(int(x) for x in info.c1)
@@ -173,13 +188,15 @@ def build_u64(keys, vals, seed: int, **opts) -> Map:
     vals = _c(vals, np.int64)
     n = keys.size
     o = _opts(**opts)
+    lam = max(1, o.keys_per_bucket)
+    nb = buckets(n, lam)
     cap = max(1, o.bound_factor * n)
-    desc = np.zeros(max(n, 1), np.uint64)
+    desc = np.zeros(max(nb, 1), np.uint64)
     slots = np.zeros(2 * cap, np.uint64)
     info = _Info()
     st = lib().or_build_u64(_p(keys), _p(vals), n, seed & (2**64 - 1), ctypes.byref(o), _p(desc),
                             _p(slots), cap, ctypes.byref(info))
-    return _finish(st, info, n, seed, desc[:n], slots, 2, "u64")
+    return _finish(st, info, n, seed, desc[:nb], slots, 2, "u64", lam=lam)
 
 
 def build_bytes(ctx, offs, vals, seed: int, **opts) -> Map:
@@ -191,13 +208,15 @@ def build_bytes(ctx, offs, vals, seed: int, **opts) -> Map:
     vals = _c(vals, np.int64)
     n = offs.size - 1
     o = _opts(**opts)
+    lam = max(1, o.keys_per_bucket)
+    nb = buckets(n, lam) if n > 0 else 0
     cap = max(1, o.bound_factor * n)
-    desc = np.zeros(max(n, 1), np.uint64)
+    desc = np.zeros(max(nb, 1), np.uint64)
     slots = np.zeros(4 * cap, np.uint64)
     info = _Info()
     st = lib().or_build_bytes(_p(ctx), _p(offs), _p(vals), n, seed & (2**64 - 1), ctypes.byref(o),
                               _p(desc), _p(slots), cap, ctypes.byref(info))
-    return _finish(st, info, n, seed, desc[:n], slots, 4, "bytes", ctx)
+    return _finish(st, info, n, seed, desc[:nb], slots, 4, "bytes", ctx, lam=lam)
 
 
 def lookup_u64(m: Map, queries, absent: int = -1):
@@ -205,7 +224,7 @@ def lookup_u64(m: Map, queries, absent: int = -1):
     out = np.empty(q.size, np.int64)
     found = np.empty(q.size, np.uint8)
     slots = np.ascontiguousarray(m.slots)
-    lib().or_lookup_u64(_p(m.desc), _p(slots), m.n, m.seed & (2**64 - 1), m.round, _p(q), q.size,
+    lib().or_lookup_u64(_p(m.desc), _p(slots), m.nb, m.seed & (2**64 - 1), m.round, _p(q), q.size,
                         absent, _p(out), _p(found))
     return out, found
 
@@ -219,16 +238,18 @@ def lookup_bytes(m: Map, qctx, qoffs, absent: int = -1):
     out = np.empty(nq, np.int64)
     found = np.empty(nq, np.uint8)
     slots = np.ascontiguousarray(m.slots)
-    lib().or_lookup_bytes(_p(m.desc), _p(slots), _p(m.ctx), m.n, m.seed & (2**64 - 1), m.round,
+    lib().or_lookup_bytes(_p(m.desc), _p(slots), _p(m.ctx), m.nb, m.seed & (2**64 - 1), m.round,
                           _p(qctx), _p(qoffs), nq, absent, _p(out), _p(found))
     return out, found
 
 
-def l1_counts(hkeys, seed: int, round_: int) -> np.ndarray:
+def l1_counts(hkeys, seed: int, round_: int, nb: int | None = None) -> np.ndarray:
+    """Keys per level-one bucket in round `round_` (nb buckets; default one per key)."""
     k = _c(hkeys, np.uint64)
-    cnt = np.zeros(k.size, np.uint32)
-    lib().or_l1_counts(_p(k), k.size, seed & (2**64 - 1), round_, _p(cnt))
-    return cnt
+    nb = k.size if nb is None else nb
+    cnt = np.zeros(max(nb, 1), np.uint32)
+    lib().or_l1_counts(_p(k), k.size, nb, seed & (2**64 - 1), round_, _p(cnt))
+    return cnt[:nb]
 
 
 def fingerprints(ctx, offs, seed: int, round_: int) -> np.ndarray:

@@ -147,14 +147,23 @@ typedef struct {
   uint64_t nonempty;
   uint32_t rounds_used;    /* rounds tried (round + 1 on success)   */
   uint32_t max_attempt;
+  uint64_t nb;             /* level-one buckets = descriptors       */
 } or_info;
 
 typedef struct {
-  uint32_t bound_factor;   /* default 4    */
+  uint32_t bound_factor;   /* default 2 * (1 + keys_per_bucket), i.e. 4 */
   uint32_t round_cap;      /* default 32   */
   uint32_t attempt_cap;    /* default 4095 */
   uint32_t reject_attempts;/* test hook: attempts below this count as failures */
+  uint32_t keys_per_bucket;/* lambda: nb = ceil(n / lambda) level-one buckets (default 1) */
 } or_opts;
+
+/* Level-one bucket count.  The paper takes one bucket per key (g k = Hash
+ * const k mod n, Sec. 2.3).  The bucket-count variant takes nb = ceil(n /
+ * lambda) buckets; the FKS argument is unchanged: E[sum s^2] = n + n (n - 1)
+ * / nb < (1 + lambda) n, so a bound of 2 (1 + lambda) n holds with
+ * probability at least 1/2 per round (Markov), as 4n does for lambda = 1. */
+static uint64_t or_buckets(uint64_t n, uint32_t lambda) { return (n + lambda - 1) / lambda; }
 
 #define OR_DUP_CHECK_AT 64u
 
@@ -258,17 +267,19 @@ static int or_build_common(const or_keys* K, const int64_t* vals, uint64_t n, ui
                            const or_opts* o, uint64_t* desc, uint64_t* slots, uint64_t slot_cap,
                            uint32_t slot_words, or_info* info, uint64_t* hkey_buf,
                            const uint8_t* ctx, const int64_t* offs) {
+  const uint64_t nb = or_buckets(n, o->keys_per_bucket);
   uint64_t* hashes = (uint64_t*)malloc(n * sizeof(uint64_t));
-  uint64_t* shape = (uint64_t*)malloc(n * sizeof(uint64_t));
-  uint64_t* gstart = (uint64_t*)malloc((n + 1) * sizeof(uint64_t));
+  uint64_t* shape = (uint64_t*)malloc(nb * sizeof(uint64_t));
+  uint64_t* gstart = (uint64_t*)malloc((nb + 1) * sizeof(uint64_t));
   uint64_t* grouped = (uint64_t*)malloc(n * sizeof(uint64_t));
-  uint64_t* cursor = (uint64_t*)malloc(n * sizeof(uint64_t));
-  uint32_t* attempt = (uint32_t*)malloc(n * sizeof(uint32_t));
+  uint64_t* cursor = (uint64_t*)malloc(nb * sizeof(uint64_t));
+  uint32_t* attempt = (uint32_t*)malloc(nb * sizeof(uint32_t));
   int status = OR_BUILD_FAILED;
   (void)slot_cap; /* checked by the callers against bound_factor * n */
   memset(info, 0, sizeof(*info));
   info->n = n;
   info->seed = seed;
+  info->nb = nb;
 
   for (uint32_t r = 0; r < o->round_cap; ++r) {
     info->rounds_used = r + 1;
@@ -277,27 +288,27 @@ static int or_build_common(const or_keys* K, const int64_t* vals, uint64_t n, ui
       for (uint64_t i = 0; i < n; ++i)
         hkey_buf[i] = or_fingerprint(ctx + offs[i], (uint64_t)(offs[i + 1] - offs[i]), base);
     }
-    /* const = Random (); hashes = Map ((mod n) . Hash const) keys */
+    /* const = Random (); hashes = Map ((mod nb) . Hash const) keys */
     uint64_t c1[3];
     or_derive(seed, r, OR_TAG_L1, 0, c1);
-    for (uint64_t i = 0; i < n; ++i) hashes[i] = or_reduce(or_hash(c1, K->hkey[i]), n);
-    /* shape = Hist n hashes (Rep n 1) */
-    memset(shape, 0, n * sizeof(uint64_t));
+    for (uint64_t i = 0; i < n; ++i) hashes[i] = or_reduce(or_hash(c1, K->hkey[i]), nb);
+    /* shape = Hist nb hashes (Rep n 1) */
+    memset(shape, 0, nb * sizeof(uint64_t));
     for (uint64_t i = 0; i < n; ++i) shape[hashes[i]] += 1;
-    /* R4: the space bound */
+    /* R4: the space bound (bound_factor * n, n = keys) */
     uint64_t S = 0;
-    for (uint64_t b = 0; b < n; ++b) S += shape[b] * shape[b];
+    for (uint64_t b = 0; b < nb; ++b) S += shape[b] * shape[b];
     if (S > (uint64_t)o->bound_factor * n) continue;
-    /* Groupby n hashes keys (stable counting sort; order is irrelevant) */
+    /* Groupby nb hashes keys (stable counting sort; order is irrelevant) */
     gstart[0] = 0;
-    for (uint64_t b = 0; b < n; ++b) gstart[b + 1] = gstart[b] + shape[b];
-    for (uint64_t b = 0; b < n; ++b) cursor[b] = gstart[b];
+    for (uint64_t b = 0; b < nb; ++b) gstart[b + 1] = gstart[b] + shape[b];
+    for (uint64_t b = 0; b < nb; ++b) cursor[b] = gstart[b];
     for (uint64_t i = 0; i < n; ++i) grouped[cursor[hashes[i]]++] = i;
     /* consts = Map make_2 (groups) */
     int any_dup = 0, any_next = 0;
     uint64_t att_sum = 0, nonempty = 0;
     uint32_t max_att = 0, max_s = 0;
-    for (uint64_t b = 0; b < n; ++b) {
+    for (uint64_t b = 0; b < nb; ++b) {
       attempt[b] = 0;
       if (shape[b] == 0) continue;
       nonempty += 1;
@@ -318,7 +329,7 @@ static int or_build_common(const or_keys* K, const int64_t* vals, uint64_t n, ui
 
     /* offsets = Presum shape^2 (exclusive, R3); descriptors */
     uint64_t off = 0;
-    for (uint64_t b = 0; b < n; ++b) {
+    for (uint64_t b = 0; b < nb; ++b) {
       desc[b] = off | (shape[b] << 32) | ((uint64_t)attempt[b] << 52);
       off += shape[b] * shape[b];
     }
@@ -342,7 +353,7 @@ static int or_build_common(const or_keys* K, const int64_t* vals, uint64_t n, ui
       }
     }
     /* R7: fill the rest of each bucket's range with its lowest occupied slot */
-    for (uint64_t b = 0; b < n; ++b) {
+    for (uint64_t b = 0; b < nb; ++b) {
       uint64_t s = shape[b];
       if (s < 2) continue;
       uint64_t lo = desc[b] & 0xFFFFFFFFull, hi = lo + s * s, first = hi;
@@ -382,7 +393,8 @@ done:
 }
 
 static void or_default_opts(or_opts* o, const or_opts* in) {
-  o->bound_factor = 4;
+  o->keys_per_bucket = (in && in->keys_per_bucket) ? in->keys_per_bucket : 1;
+  o->bound_factor = 2 * (1 + o->keys_per_bucket);
   o->round_cap = 32;
   o->attempt_cap = 4095;
   o->reject_attempts = 0;
@@ -394,25 +406,35 @@ static void or_default_opts(or_opts* o, const or_opts* in) {
   }
 }
 
-/* Build over uint64 keys.  desc[n], slots[2 * slot_cap] (uint64 words). */
+/* Sizes every build accepts: n keys below 2^30, lambda in 1 .. 16, and a
+ * slot range whose offsets fit the descriptor's 32-bit field. */
+static int or_sizes_ok(const or_opts* o, uint64_t n, uint64_t slot_cap) {
+  if (n == 0 || n >= (1ull << 30)) return 0;
+  if (o->keys_per_bucket < 1 || o->keys_per_bucket > 16) return 0;
+  if ((uint64_t)o->bound_factor * n > 0xFFFFFFFFull) return 0;
+  return slot_cap >= (uint64_t)o->bound_factor * n;
+}
+
+/* Build over uint64 keys.  desc[nb], slots[2 * slot_cap] (uint64 words),
+ * nb = ceil(n / keys_per_bucket). */
 int or_build_u64(const uint64_t* keys, const int64_t* vals, uint64_t n, uint64_t seed,
                  const or_opts* opts, uint64_t* desc, uint64_t* slots, uint64_t slot_cap,
                  or_info* info) {
   or_opts o;
   or_default_opts(&o, opts);
-  if (n == 0 || n >= (1ull << 30) || slot_cap < (uint64_t)o.bound_factor * n) return OR_INVALID_ARG;
+  if (!or_sizes_ok(&o, n, slot_cap)) return OR_INVALID_ARG;
   or_keys K = {keys, NULL, NULL};
   return or_build_common(&K, vals, n, seed, &o, desc, slots, slot_cap, 2, info, NULL, NULL, NULL);
 }
 
 /* Build over byte-string keys: key i is ctx[offs[i] .. offs[i+1]).
- * desc[n], slots[4 * slot_cap] (uint64 words). */
+ * desc[nb], slots[4 * slot_cap] (uint64 words). */
 int or_build_bytes(const uint8_t* ctx, const int64_t* offs, const int64_t* vals, uint64_t n,
                    uint64_t seed, const or_opts* opts, uint64_t* desc, uint64_t* slots,
                    uint64_t slot_cap, or_info* info) {
   or_opts o;
   or_default_opts(&o, opts);
-  if (n == 0 || n >= (1ull << 30) || slot_cap < (uint64_t)o.bound_factor * n) return OR_INVALID_ARG;
+  if (!or_sizes_ok(&o, n, slot_cap)) return OR_INVALID_ARG;
   for (uint64_t i = 0; i < n; ++i) {
     int64_t len = offs[i + 1] - offs[i];
     if (offs[i] < 0 || len < 0 || len >= (1ll << 24) || offs[i + 1] >= (1ll << 40))
@@ -426,15 +448,16 @@ int or_build_bytes(const uint8_t* ctx, const int64_t* offs, const int64_t* vals,
 }
 
 /* Lookup (Sec. 2.2 membership test; Sec. 3.2 lookup -> opt v).
+ * nb = the map's level-one buckets (n for the paper's construction).
  * found[i] = 1 and out[i] = value for members, found[i] = 0 and
  * out[i] = absent otherwise. */
-void or_lookup_u64(const uint64_t* desc, const uint64_t* slots, uint64_t n, uint64_t seed,
+void or_lookup_u64(const uint64_t* desc, const uint64_t* slots, uint64_t nb, uint64_t seed,
                    uint32_t round, const uint64_t* q, uint64_t nq, int64_t absent,
                    int64_t* out, uint8_t* found) {
   uint64_t c1[3];
   or_derive(seed, round, OR_TAG_L1, 0, c1);
   for (uint64_t i = 0; i < nq; ++i) {
-    uint64_t b = or_reduce(or_hash(c1, q[i]), n);
+    uint64_t b = or_reduce(or_hash(c1, q[i]), nb);
     uint64_t d = desc[b], s = (d >> 32) & 0xFFFFF;
     int hit = 0;
     int64_t v = absent;
@@ -451,7 +474,7 @@ void or_lookup_u64(const uint64_t* desc, const uint64_t* slots, uint64_t n, uint
 
 /* Lookup of byte-string needles: needle i is qctx[qoffs[i] .. qoffs[i+1]);
  * the map's own context is mctx (the needle context may differ, Sec. 3.1). */
-void or_lookup_bytes(const uint64_t* desc, const uint64_t* slots, const uint8_t* mctx, uint64_t n,
+void or_lookup_bytes(const uint64_t* desc, const uint64_t* slots, const uint8_t* mctx, uint64_t nb,
                      uint64_t seed, uint32_t round, const uint8_t* qctx, const int64_t* qoffs,
                      uint64_t nq, int64_t absent, int64_t* out, uint8_t* found) {
   uint64_t c1[3];
@@ -460,7 +483,7 @@ void or_lookup_bytes(const uint64_t* desc, const uint64_t* slots, const uint8_t*
   for (uint64_t i = 0; i < nq; ++i) {
     uint64_t len = (uint64_t)(qoffs[i + 1] - qoffs[i]);
     uint64_t fp = or_fingerprint(qctx + qoffs[i], len, base);
-    uint64_t b = or_reduce(or_hash(c1, fp), n);
+    uint64_t b = or_reduce(or_hash(c1, fp), nb);
     uint64_t d = desc[b], s = (d >> 32) & 0xFFFFF;
     int hit = 0;
     int64_t v = absent;
@@ -480,13 +503,14 @@ void or_lookup_bytes(const uint64_t* desc, const uint64_t* slots, const uint8_t*
   }
 }
 
-/* Level-one histogram of one round (for kernel-level parity checks). */
-void or_l1_counts(const uint64_t* hkeys, uint64_t n, uint64_t seed, uint32_t round,
+/* Level-one histogram of one round over nb buckets (for kernel-level
+ * parity checks). */
+void or_l1_counts(const uint64_t* hkeys, uint64_t n, uint64_t nb, uint64_t seed, uint32_t round,
                   uint32_t* cnt) {
   uint64_t c1[3];
   or_derive(seed, round, OR_TAG_L1, 0, c1);
-  memset(cnt, 0, n * sizeof(uint32_t));
-  for (uint64_t i = 0; i < n; ++i) cnt[or_reduce(or_hash(c1, hkeys[i]), n)] += 1;
+  memset(cnt, 0, nb * sizeof(uint32_t));
+  for (uint64_t i = 0; i < n; ++i) cnt[or_reduce(or_hash(c1, hkeys[i]), nb)] += 1;
 }
 
 /* Fingerprints of n strings for one round (for kernel-level parity checks). */

@@ -54,7 +54,7 @@ def np_reduce(h, m):
 def slot_index(m: O.Map, hkeys):
     """h k of Sec. 2.2 for every key, from the map's descriptors."""
     c1 = [np.uint64(x) for x in O.derive(m.seed, m.round, O.TAG_L1, 0)]
-    b = np_reduce(np_hash(c1, hkeys), m.n).astype(np.int64)
+    b = np_reduce(np_hash(c1, hkeys), m.nb).astype(np.int64)
     off, s, att = O.desc_fields(m.desc)
     c2 = np_derive(m.seed, m.round, b.astype(np.uint64), att[b].astype(np.uint64))
     j = off[b] + np_reduce(np_hash(c2, hkeys), (s[b] * s[b]).astype(np.uint64)).astype(np.int64)
@@ -187,19 +187,22 @@ def test_fingerprint_separates_padding_and_length():
 
 
 # ------------------------------------------------------------------ construction
-def check_table(m: O.Map, keys, vals):
+def check_table(m: O.Map, keys, vals, bound=None):
     """Well-formed and collision-free (Sec. 2.2), S bound, layout, fill rule."""
     n = len(keys)
+    lam = m.keys_per_bucket
+    bound = bound or 2 * (1 + lam)
     off, s, att = O.desc_fields(m.desc)
     assert m.status == O.OK
+    assert m.nb == -(-n // lam) == s.size
     assert s.sum() == n
-    assert m.S == int((s * s).sum()) <= 4 * n
+    assert m.S == int((s * s).sum()) <= bound * n
     # offsets = exclusive presum of shape^2
     assert off[0] == 0 and np.array_equal(off[1:], np.cumsum(s * s)[:-1])
     assert (att[s <= 1] == 0).all()
     b, j = slot_index(m, keys)
-    # the level-one histogram is Hist n (Map g K)
-    assert np.array_equal(np.bincount(b, minlength=n), s)
+    # the level-one histogram is Hist nb (Map g K)
+    assert np.array_equal(np.bincount(b, minlength=m.nb), s)
     assert (j >= 0).all() and (j < m.S).all()            # property 1
     assert np.unique(j).size == n                         # property 2
     assert np.array_equal(m.slots[j, 0], np.asarray(keys, np.uint64))
@@ -394,3 +397,90 @@ def test_binary_search_matches_searchsorted():
         i = int(np.searchsorted(a, q))
         want = i if i < a.size and a[i] == q else -1
         assert O.binary_search(a, int(q)) == want
+
+
+# ------------------------------------------------------------------ bucket-count variant
+# nb = ceil(n / lambda) level-one buckets instead of n; everything else is
+# the paper's construction.  The FKS analysis gives E[sum s^2] = n + n (n - 1)
+# / nb for a random level-one hash, and the default bound 2 (1 + lambda) n.
+@pytest.mark.parametrize("lam", [2, 4, 8, 16])
+@pytest.mark.parametrize("n", [1, 5, 17, 1000, 4099, 1 << 15])
+def test_bucket_variant_invariants(lam, n):
+    w = W.u64_workload(n, 2 * n, 0.5, seed=n + lam)
+    m = O.build_u64(w.keys, w.vals, seed=lam * 7 + 1, keys_per_bucket=lam)
+    assert m.nb == (n + lam - 1) // lam and m.desc.size == m.nb
+    check_table(m, w.keys, w.vals)
+    out, found = O.lookup_u64(m, w.queries, absent=-7)
+    assert np.array_equal(found, w.expect_found)
+    assert np.array_equal(out, np.where(w.expect_found == 1, w.expect_vals, -7))
+
+
+def test_bucket_variant_lambda1_is_the_paper_build():
+    w = W.u64_workload(3000, 10, 0.5, seed=3)
+    a = O.build_u64(w.keys, w.vals, seed=9)
+    b = O.build_u64(w.keys, w.vals, seed=9, keys_per_bucket=1, bound_factor=4)
+    assert a.nb == b.nb == 3000
+    assert np.array_equal(a.desc, b.desc) and np.array_equal(a.slots, b.slots)
+
+
+@pytest.mark.parametrize("lam", [2, 4, 8, 16])
+def test_bucket_variant_statistics(lam):
+    """Mean S / n over seeds against 1 + (n - 1) / nb; a reduction over n
+    buckets instead of nb would give about 2."""
+    n = 4096
+    nb = n // lam
+    ratios = []
+    for seed in range(30):
+        keys = W.key_stream(500 + seed, n)
+        m = O.build_u64(keys, np.arange(n), seed=seed, keys_per_bucket=lam)
+        assert m.status == O.OK
+        if m.rounds_used == 1:
+            ratios.append(m.S / n)
+    expect = 1 + (n - 1) / nb
+    assert abs(np.mean(ratios) - expect) < 0.04 * expect
+
+
+@pytest.mark.parametrize("lam", [2, 8, 16])
+def test_bucket_variant_brute_force(lam):
+    rng = np.random.default_rng(lam)
+    for trial in range(120):
+        n = int(rng.integers(1, 97))
+        keys = np.unique(rng.integers(0, 2**64, n, dtype=np.uint64, endpoint=False))
+        rng.shuffle(keys)
+        vals = rng.integers(-2**62, 2**62, keys.size)
+        m = O.build_u64(keys, vals, seed=int(rng.integers(0, 2**63)), keys_per_bucket=lam)
+        assert m.status == O.OK
+        d = dict(zip(keys.tolist(), vals.tolist()))
+        probes = np.concatenate([keys, rng.integers(0, 2**64, 64, dtype=np.uint64)])
+        out, found = O.lookup_u64(m, probes, absent=-1)
+        for q, v, f in zip(probes.tolist(), out.tolist(), found.tolist()):
+            assert f == (q in d)
+            assert v == d.get(q, -1)
+
+
+def test_bucket_variant_l1_counts_and_bounds():
+    keys = W.key_stream(8, 5000)
+    for lam in (1, 4, 16):
+        nb = -(-5000 // lam)
+        cnt = O.l1_counts(keys, seed=4, round_=2, nb=nb)
+        c1 = [np.uint64(x) for x in O.derive(4, 2, O.TAG_L1, 0)]
+        b = np_reduce(np_hash(c1, keys), np.uint64(nb)).astype(np.int64)
+        assert np.array_equal(cnt, np.bincount(b, minlength=nb))
+    # a bound below E[S] / n forces redraws; far below it, failure
+    m = O.build_u64(keys[:300], np.arange(300), seed=1, keys_per_bucket=8, bound_factor=9, round_cap=200)
+    assert m.status == O.OK and m.S <= 9 * 300 and m.rounds_used >= 1
+    m = O.build_u64(keys[:300], np.arange(300), seed=1, keys_per_bucket=8, bound_factor=2, round_cap=5)
+    assert m.status == O.BUILD_FAILED
+    # sizes outside what the descriptor encodes
+    assert O.build_u64(keys[:10], np.arange(10), seed=1, keys_per_bucket=17).status == O.INVALID_ARG
+    assert O.build_u64(keys[:10], np.arange(10), seed=1, keys_per_bucket=3).status == O.OK
+
+
+@pytest.mark.parametrize("lam", [4, 16])
+def test_bucket_variant_strings(lam):
+    w = W.string_workload(3000, 2000, 0.5, seed=lam)
+    m = O.build_bytes(w.ctx, w.offs, w.vals, seed=5, keys_per_bucket=lam)
+    assert m.status == O.OK and m.nb == -(-3000 // lam)
+    out, found = O.lookup_bytes(m, w.qctx, w.qoffs, absent=-3)
+    assert np.array_equal(found, w.expect_found)
+    assert np.array_equal(out, np.where(w.expect_found == 1, w.expect_vals, -3))
