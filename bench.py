@@ -303,6 +303,37 @@ def run_batched(F, W, torch, hbm):
             "lookup_frac": lq * q.numel() / (lms / 1e3) / 1e9 / hbm, "results_match_truth": bool(ok)}
 
 
+def run_bucket_variants(F, torch, hbm, keys, vals, queries, out, found, w, n, nq):
+    """The level-one bucket-count variant on the headline workload: nb =
+    ceil(n / lambda) buckets for lambda in 1, 2, 4, 8, 16 (1 is the paper's
+    construction).  Fewer buckets keep the descriptor array (8 nb bytes) in
+    L2, so lookups approach one DRAM access per query; the slot array grows
+    to about (1 + lambda) n slots."""
+    stream = torch.cuda.current_stream()
+    res = {}
+    for lam in (1, 2, 4, 8, 16):
+        o = F.make_opts(keys_per_bucket=lam)
+        bms = _timed(torch, stream, lambda: F.fks_build_u64(keys, vals, SEED, o))
+        m = F.fks_build_u64(keys, vals, SEED, o)
+        lms = _timed(torch, stream, lambda: F.fks_lookup_u64(m, queries, out, found, -1))
+        ok = np.array_equal(found.cpu().numpy(), w.expect_found) and \
+            np.array_equal(out.cpu().numpy(), np.where(w.expect_found == 1, w.expect_vals, -1))
+        info = F.fks_map_info(m)
+        ne = info.nonempty_buckets / info.buckets
+        lq = lookup_bytes_per_query(HIT, ne)
+        res[str(lam)] = {
+            "buckets": int(info.buckets), "descriptor_MB": info.buckets * 8 / 1e6,
+            "S_over_n": info.slots / n, "map_bytes_per_key": info.bytes / n,
+            "build_ms": bms, "lookup_ms": lms, "step_ms": bms + lms,
+            "build_keys_per_s": n / (bms / 1e3), "lookups_per_s": nq / (lms / 1e3),
+            "keys_plus_lookups_per_s": (n + nq) / ((bms + lms) / 1e3),
+            "lookup_bytes_model": f"{lq:.2f} B/query", "lookup_GBps": lq * nq / (lms / 1e3) / 1e9,
+            "lookup_frac": lq * nq / (lms / 1e3) / 1e9 / hbm, "results_match_truth": bool(ok)}
+        del m
+        torch.cuda.empty_cache()
+    return res
+
+
 def run_serving(args, F, W, torch):
     """Config 5: a Poisson stream of build and lookup requests (90 % lookups of
     log-uniform size in [1, 2^16], 80 % hits; 10 % builds, half uint64 maps of
@@ -589,6 +620,7 @@ def main():
             "fks_speedup_build": med(sb) / med(build_ms), "fks_speedup_lookup": med(sl) / lk}
     # ---- the other rows of the path: string keys (config 3), batched maps (config 4)
     if not args.no_extras:
+        line["bucket_variants"] = run_bucket_variants(F, torch, hbm, keys, vals, queries, out, found, w, n, nq)
         line["strings"] = run_strings(F, W, torch, hbm)
         line["batched"] = run_batched(F, W, torch, hbm)
     # ---- serving stream (config 5): continuous batching against per-call launches

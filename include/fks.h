@@ -70,14 +70,28 @@ typedef struct {
   void* user;
 } fks_allocator;
 
-/* Build options; a NULL pointer or a 0 field selects the default. */
+/* Build options; a NULL pointer or a 0 field selects the default.
+ *
+ * keys_per_bucket (lambda) selects the level-one bucket count: the paper
+ * draws one bucket per key (g k = Hash const k mod n, Sec. 2.3); lambda in
+ * {2, 4, 8, 16} draws nb = ceil(n / lambda) buckets and keeps every other
+ * step.  Fewer buckets mean a smaller descriptor array (8 nb bytes), which
+ * stays in L2 for large maps, so a lookup costs about one DRAM miss instead
+ * of the paper's two (Sec. 5) -- at the price of more slots: E[sum s^2] =
+ * n + n (n - 1) / nb, about (1 + lambda) n.  The default bound_factor is
+ * 2 (1 + lambda) (4 for lambda = 1), twice that expectation, so each
+ * level-one round passes the space bound with probability >= 1/2 as in the
+ * paper's analysis.  bound_factor * n must stay below 2^32 (slot offsets
+ * are 32-bit descriptor fields); larger builds return FKS_ERR_INVALID_ARG.
+ * A struct_size that ends before keys_per_bucket is accepted (lambda 1). */
 typedef struct {
   size_t struct_size;        /* sizeof(fks_build_opts)                          */
-  uint32_t bound_factor;     /* level-one redraw when sum s^2 > bound*n (4)     */
+  uint32_t bound_factor;     /* level-one redraw when sum s^2 > bound*n (2 (1 + lambda)) */
   uint32_t attempt_cap;      /* level-two attempts per bucket and round (4095) */
   uint32_t round_cap;        /* level-one rounds (32)                           */
   uint32_t reject_attempts;  /* TEST HOOK: attempts below this count as failed (0) */
   uint32_t spin_limit;       /* bound of every device wait, in polls (1<<20)     */
+  uint32_t keys_per_bucket;  /* lambda: 1 (the paper), 2, 4, 8 or 16 (1)        */
 } fks_build_opts;
 
 typedef struct {
@@ -95,6 +109,9 @@ typedef struct {
   uint32_t val_type;      /* fks_val_type                             */
   uint32_t overflow_partitions; /* partitions built through global memory */
   uint64_t nonempty_buckets;    /* buckets with s > 0                      */
+  uint64_t buckets;             /* level-one buckets nb = descriptors      */
+  uint32_t keys_per_bucket;     /* lambda of the build                     */
+  uint32_t reserved;
 } fks_map_info_t;
 
 /* Phase timings of the last build on the calling thread (CUDA events on the
@@ -202,7 +219,9 @@ fks_map_t fks_mapset_get(fks_mapset_t set, uint32_t j);
  * library (about 8.4 MB, held on every GPU that loads the library until the
  * process exits).  Hence n <= FKS_NOALLOC_MAX_KEYS; larger n returns
  * FKS_ERR_INVALID_ARG.
- *   keys, vals, val_type, n, seed, opts   as for fks_build_u64
+ *   keys, vals, val_type, n, seed, opts   as for fks_build_u64, with one
+ *                  level-one bucket per key (keys_per_bucket other than 0
+ *                  or 1 returns FKS_ERR_INVALID_ARG; bound_factor <= 4)
  *   desc_out       uint64[n] (device): the bucket descriptors
  *   slots_out      slot_capacity slots of 16 bytes (device), slot_capacity >=
  *                  bound_factor * n; the first info.slots slots are the table
@@ -323,7 +342,7 @@ void fks_server_destroy(fks_server_t srv);
 fks_status fks_map_info(fks_map_t map, fks_map_info_t* h_out);
 
 /* fks_map_export -- copy the tables to host memory (synchronises `stream`):
- *   h_desc   uint64[n]   bucket descriptors: slot offset (bits 0..31) | s
+ *   h_desc   uint64[buckets] bucket descriptors (info.buckets of them): slot offset (bits 0..31) | s
  *            (bits 32..51) | level-two attempt (bits 52..63)
  *   h_slots  S slots: uint64 maps {key, value} (16 B); string maps {fp,
  *            offset | length << 40, value, 0} (32 B); empty slots hold the

@@ -174,6 +174,8 @@ struct fks_map {
   fks_val_type vt = FKS_VAL_I64;
   uint64_t n = 0, seed = 0, S = 0, slot_cap = 0, att_sum = 0, ctx_bytes = 0, bytes = 0;
   uint64_t nonempty = 0;
+  uint64_t nb = 0;          // level-one buckets (= descriptors)
+  uint32_t lambda = 1;      // keys per bucket of the level-one draw
   uint32_t round = 0, max_s = 0, max_att = 0, overflow = 0;
   HashConsts c1{};
   uint64_t fpb = 0;
@@ -214,7 +216,7 @@ static LookupMap lookup_view(const fks_map& m) {
   L.c1 = m.c1;
   L.seed = m.seed;
   L.fpb = m.fpb;
-  L.n = uint32_t(m.n);
+  L.nb = uint32_t(m.nb);
   L.round = m.round;
   return L;
 }
@@ -222,20 +224,35 @@ static LookupMap lookup_view(const fks_map& m) {
 // ---------------------------------------------------------------- options
 struct Opts {
   uint32_t bound = 4, attempt_cap = 4095, round_cap = 32, reject = 0, spin = 1u << 20, hold = 0;
+  uint32_t lambda = 1;  // keys per level-one bucket
 };
 
+// Options of the older, shorter layout (without keys_per_bucket) are accepted.
 static bool read_opts(const fks_build_opts* o, Opts* out) {
   if (!o) return true;
   if (o->struct_size < offsetof(fks_build_opts, spin_limit) + sizeof(uint32_t)) return false;
+  if (o->struct_size >= offsetof(fks_build_opts, keys_per_bucket) + sizeof(uint32_t) && o->keys_per_bucket)
+    out->lambda = o->keys_per_bucket;
+  if (out->lambda != 1 && out->lambda != 2 && out->lambda != 4 && out->lambda != 8 && out->lambda != 16)
+    return false;
+  out->bound = 2 * (1 + out->lambda);  // E[sum s^2] < (1 + lambda) n: bound = twice that
   if (o->bound_factor) out->bound = o->bound_factor;
   if (o->attempt_cap) out->attempt_cap = o->attempt_cap;
   if (o->round_cap) out->round_cap = o->round_cap;
   out->reject = o->reject_attempts;
   if (o->spin_limit) out->spin = o->spin_limit;
-  if (out->attempt_cap > 4095 || out->round_cap > 65535 || out->bound < 1 || out->bound > 4)
+  if (out->attempt_cap > 4095 || out->round_cap > 65535 || out->bound < 1 || out->bound > 64)
     return false;
   return true;
 }
+
+// Buckets of up to this many keys are searched by a single thread, larger
+// ones by packed warp segments (measured on 2^26-key builds: 3 for small
+// buckets; with 8 or 16 keys per bucket every bucket goes to a segment).
+static uint32_t thread_search_max(uint32_t lambda) { return lambda <= 4 ? 3u : 1u; }
+
+// Slot offsets are 32-bit descriptor fields: bound * n must stay below 2^32.
+static bool sizes_fit(const Opts& o, uint64_t n) { return uint64_t(o.bound) * n <= 0xFFFFFFFFull; }
 
 // test hook (not in the public header): make partition 0 never publish its
 // slot prefix so that the bounded wait of partition 1 runs out.
@@ -263,6 +280,7 @@ struct SetMem {
   uint64_t* slots = nullptr;
   uint8_t* ctx = nullptr;
   std::vector<uint64_t> slot_base;  // per map
+  std::vector<uint64_t> desc_base;  // per map
 };
 
 static fks_status build_impl(const BuildIn& in, const Opts& o, const Alloc& A, cudaStream_t st,
@@ -273,11 +291,18 @@ static fks_status build_impl(const BuildIn& in, const Opts& o, const Alloc& A, c
   const int PW = str ? 2 : 1;
   const int W = str ? 4 : 2;  // words per slot
   const uint64_t total = uint64_t(in.seg[m]);
-  uint64_t slot_total = 0;
-  std::vector<uint64_t> slot_base(m);
+  const uint32_t logB = part_log_buckets(o.lambda);
+  const uint64_t B = 1ull << logB;
+  uint64_t slot_total = 0, desc_total = 0;
+  std::vector<uint64_t> slot_base(m), desc_base(m), nbs(m);
   for (uint32_t j = 0; j < m; ++j) {
+    const uint64_t n = uint64_t(in.seg[j + 1] - in.seg[j]);
+    if (!sizes_fit(o, n)) return fail(FKS_ERR_INVALID_ARG, "bound_factor * n does not fit 32-bit slot offsets");
     slot_base[j] = slot_total;
-    slot_total += uint64_t(o.bound) * uint64_t(in.seg[j + 1] - in.seg[j]);
+    slot_total += uint64_t(o.bound) * n;
+    nbs[j] = level1_buckets(n, o.lambda);
+    desc_base[j] = desc_total;
+    desc_total += nbs[j];
   }
   // context bytes: offs[total] from the device
   uint64_t ctx_bytes = 0;
@@ -290,7 +315,7 @@ static fks_status build_impl(const BuildIn& in, const Opts& o, const Alloc& A, c
   }
   // the set's own memory: descriptors, slots, context copy
   Carve cm;
-  const size_t o_desc = cm.take<uint64_t>(total);
+  const size_t o_desc = cm.take<uint64_t>(desc_total);
   const size_t o_slots = cm.take<uint64_t>(slot_total * W);
   const size_t o_ctx = cm.take<uint8_t>(str ? ctx_bytes + 16 : 0);
   uint8_t* block = static_cast<uint8_t*>(A.get(cm.off, st));
@@ -299,6 +324,7 @@ static fks_status build_impl(const BuildIn& in, const Opts& o, const Alloc& A, c
   mem->slots = reinterpret_cast<uint64_t*>(block + o_slots);
   mem->ctx = str ? block + o_ctx : nullptr;
   mem->slot_base = slot_base;
+  mem->desc_base = desc_base;
   if (str && ctx_bytes) {
     cudaError_t e = cudaMemcpyAsync(mem->ctx, in.ctx, ctx_bytes, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) {
@@ -308,8 +334,7 @@ static fks_status build_impl(const BuildIn& in, const Opts& o, const Alloc& A, c
   }
   // scratch for the largest pass (the first one holds every map)
   uint64_t P_all = 0;
-  for (uint32_t j = 0; j < m; ++j)
-    P_all += (uint64_t(in.seg[j + 1] - in.seg[j]) + kB - 1) / kB;
+  for (uint32_t j = 0; j < m; ++j) P_all += (nbs[j] + B - 1) / B;
   Carve cs;
   const size_t s_cnt = cs.take<uint32_t>(P_all + 1);
   const size_t s_start = cs.take<uint32_t>(P_all + 1);
@@ -375,10 +400,12 @@ static fks_status build_impl(const BuildIn& in, const Opts& o, const Alloc& A, c
   p.ctx = mem->ctx;
   p.desc = mem->desc;
   p.slots = mem->slots;
+  p.logB = logB;
   p.cfg.attempt_cap = o.attempt_cap;
   p.cfg.reject = o.reject;
   p.cfg.spin_limit = o.spin;
   p.cfg.hold_first = uint32_t(g_hold_first_partition);
+  p.cfg.thread_max = thread_search_max(o.lambda);
 
   std::vector<uint32_t> round(m, 0);
   std::vector<uint32_t> active(m);
@@ -414,19 +441,20 @@ static fks_status build_impl(const BuildIn& in, const Opts& o, const Alloc& A, c
       MapDev& M = h_maps[a];
       M.key_begin = uint64_t(in.seg[j]);
       M.pass_begin = pe;
-      M.desc_base = uint64_t(in.seg[j]);
+      M.desc_base = desc_base[j];
       M.slot_base = slot_base[j];
       M.seed = in.seeds[j];
       M.round = round[j];
       M.c1 = derive(M.seed, M.round, kTagLevel1, 0);
       M.fpb = fp_base(M.seed, M.round);
       M.n = uint32_t(n);
+      M.nb = uint32_t(nbs[j]);
       M.slot_cap = uint32_t(uint64_t(o.bound) * n);
       M.part_begin = pp;
       h_pseg[a] = pe;
       h_qseg[a] = pp;
       pe += n;
-      pp += uint32_t((n + kB - 1) / kB);
+      pp += uint32_t((nbs[j] + B - 1) / B);
     }
     h_pseg[ma] = pe;
     h_qseg[ma] = pp;
@@ -535,11 +563,13 @@ static fks_status build_impl(const BuildIn& in, const Opts& o, const Alloc& A, c
       M.max_att = S.max_att;
       M.overflow = S.overflow;
       M.nonempty = S.nonempty;
-      M.desc = mem->desc + in.seg[j];
+      M.nb = nbs[j];
+      M.lambda = o.lambda;
+      M.desc = mem->desc + desc_base[j];
       M.slots = mem->slots + slot_base[j] * W;
       M.ctx = mem->ctx;
       M.ctx_bytes = ctx_bytes;
-      M.bytes = sizeof(uint64_t) * (M.n + W * M.slot_cap);
+      M.bytes = sizeof(uint64_t) * (M.nb + W * M.slot_cap);
     }
     active.swap(next);
   }
@@ -738,13 +768,13 @@ fks_status fks_build_batched(fks_key_kind kind, const uint64_t* keys, const uint
     if (per[j] == FKS_OK) tab[j] = lookup_view(set->maps[j]);
     else {
       memset(&tab[j], 0, sizeof(LookupMap));
-      tab[j].desc = mem.desc + h_seg[j];
-      tab[j].n = 1;  // a single empty bucket
+      tab[j].desc = mem.desc + mem.desc_base[j];
+      tab[j].nb = 1;  // a single empty bucket
     }
   }
   // failed maps: make their first descriptor an empty bucket
   for (uint32_t j = 0; j < m; ++j)
-    if (per[j] != FKS_OK) cudaMemsetAsync(mem.desc + h_seg[j], 0, sizeof(uint64_t), st);
+    if (per[j] != FKS_OK) cudaMemsetAsync(mem.desc + mem.desc_base[j], 0, sizeof(uint64_t), st);
   set->d_table = static_cast<LookupMap*>(A.get(sizeof(LookupMap) * m, st));
   if (!set->d_table) {
     fks_mapset_destroy(set);
@@ -803,6 +833,8 @@ fks_status fks_map_info(fks_map_t map, fks_map_info_t* h_out) {
   h_out->val_type = map->vt;
   h_out->overflow_partitions = map->overflow;
   h_out->nonempty_buckets = map->nonempty;
+  h_out->buckets = map->nb;
+  h_out->keys_per_bucket = map->lambda;
   return FKS_OK;
 }
 
@@ -811,7 +843,7 @@ fks_status fks_map_export(fks_map_t map, uint64_t* h_desc, void* h_slots, uint8_
   if (!map) return fail(FKS_ERR_INVALID_ARG, "fks_map_export: NULL map");
   const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int W = map->kind == FKS_KEY_BYTES ? 4 : 2;
-  if (h_desc) FKS_CUDA(cudaMemcpyAsync(h_desc, map->desc, sizeof(uint64_t) * map->n, cudaMemcpyDeviceToHost, st));
+  if (h_desc) FKS_CUDA(cudaMemcpyAsync(h_desc, map->desc, sizeof(uint64_t) * map->nb, cudaMemcpyDeviceToHost, st));
   if (h_slots && map->S)
     FKS_CUDA(cudaMemcpyAsync(h_slots, map->slots, sizeof(uint64_t) * W * map->S, cudaMemcpyDeviceToHost, st));
   if (h_ctx && map->kind == FKS_KEY_BYTES && map->ctx_bytes)

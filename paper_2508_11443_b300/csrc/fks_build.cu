@@ -6,8 +6,10 @@
 // same steps are arranged around the memory hierarchy:
 //
 //   pass 1  k_partition<count>   g k for every key; keys per partition of
-//                                kB = 1024 consecutive buckets (L2 atomics on
-//                                a small counter array, warp-aggregated)
+//                                2^logB consecutive buckets (1024 with one
+//                                bucket per key; about 1024 keys in any
+//                                case), L2 atomics on a small counter array,
+//                                warp-aggregated
 //   pass 2  k_scan_parts         exclusive scan of the partition counts
 //   pass 3  k_partition<scatter> keys (+ payload) scattered into contiguous
 //                                partition ranges
@@ -165,7 +167,8 @@ __global__ void __launch_bounds__(256) k_partition(PassDev p, int agg) {
   // the one-map case keeps its parameters in registers
   const uint64_t kb0 = maps[0].key_begin, pb0 = maps[0].pass_begin;
   const HashConsts c10 = maps[0].c1;
-  const uint32_t n0 = maps[0].n, part0 = maps[0].part_begin;
+  const uint32_t n0 = maps[0].nb, part0 = maps[0].part_begin;
+  const uint32_t logB = p.logB;
   const uint64_t* __restrict__ hkeys = p.hkeys;
   for (uint64_t base = warp0; base < p.total; base += stride) {
     uint64_t k[kUnroll], in[kUnroll], pv[kUnroll], po[kUnroll];
@@ -179,13 +182,13 @@ __global__ void __launch_bounds__(256) k_partition(PassDev p, int agg) {
       if (p.m == 1) {
         in[u] = kb0 + (e - pb0);
         k[u] = ok[u] ? __ldcs(reinterpret_cast<const unsigned long long*>(hkeys) + in[u]) : 0;
-        gp[u] = part0 + (reduce32(hash32(c10, k[u]), n0) >> kLogB);
+        gp[u] = part0 + (reduce32(hash32(c10, k[u]), n0) >> logB);
       } else {
         const uint32_t j = ok[u] ? upper_seg(seg, p.m, e) : 0u;
         in[u] = maps[j].key_begin + (e - maps[j].pass_begin);
         k[u] = ok[u] ? __ldcs(reinterpret_cast<const unsigned long long*>(hkeys) + in[u]) : 0;
         const HashConsts c1 = maps[j].c1;
-        gp[u] = maps[j].part_begin + (reduce32(hash32(c1, k[u]), maps[j].n) >> kLogB);
+        gp[u] = maps[j].part_begin + (reduce32(hash32(c1, k[u]), maps[j].nb) >> logB);
       }
       if (kScatter && ok[u]) {  // payload loads issued before the claims
         pv[u] = uint64_t(load_val(p.vals, p.vals_i64, in[u]));
@@ -281,7 +284,8 @@ struct Smem {
 struct PartCtl {
   uint32_t gp, skip, nbig, maxs, maxatt, flag_a, flag_b, nonempty;
   uint32_t failed;  // a bucket found no constants: this pass of the map is discarded
-  uint32_t nwork;   // entries of the search worklist
+  uint32_t nwork;
+  uint32_t ccnt[8], cbase[8], ccur[8];  // search classes: list sizes, starts, cursors
   uint32_t next_gp, next_issued, abort;
   uint64_t excl, Spart, attsum;
   unsigned long long fillmin;  // (slot << 32) | member of a CTA-searched bucket
@@ -292,7 +296,7 @@ struct PartCtl {
 struct MapRegs {
   HashConsts c1;
   uint64_t seed, desc_base, slot_base;
-  uint32_t n, round, slot_cap, part_begin, part_end;
+  uint32_t nb, round, slot_cap, part_begin, part_end;  // nb: level-one buckets
 };
 
 __device__ __forceinline__ MapRegs load_map(const PassDev& p, uint32_t j) {
@@ -302,7 +306,7 @@ __device__ __forceinline__ MapRegs load_map(const PassDev& p, uint32_t j) {
   r.seed = M.seed;
   r.desc_base = M.desc_base;
   r.slot_base = M.slot_base;
-  r.n = M.n;
+  r.nb = M.nb;
   r.round = M.round;
   r.slot_cap = M.slot_cap;
   r.part_begin = M.part_begin;
@@ -362,17 +366,18 @@ __device__ uint32_t issue_stage(const PassDev& p, uint32_t gp, uint64_t* raw_key
   return 1;
 }
 
-// Exclusive Presum of s and s^2 over the partition's buckets (cnt[] holds s).
-// Leaves gst[] the group starts (gst[kB] = keys), soff[] the partition-local
-// slot offsets, ctl.Spart = sum s^2, ctl.maxs, ctl.nonempty.
-__device__ void scan_buckets(const uint32_t* cnt, uint32_t* gst, uint32_t* soff, PartCtl& ctl) {
+// Exclusive Presum of s and s^2 over the partition's nb <= kB buckets
+// (cnt[] holds s).  Leaves gst[] the group starts (gst[nb] = keys), soff[]
+// the partition-local slot offsets, ctl.Spart = sum s^2, ctl.maxs,
+// ctl.nonempty.
+__device__ void scan_buckets(const uint32_t* cnt, uint32_t* gst, uint32_t* soff, PartCtl& ctl, uint32_t nb) {
   const uint32_t t = threadIdx.x;
   constexpr uint32_t kPer = kB / kPartThreads;
   uint32_t c[kPer], ls = 0, mx = 0, ne = 0;
   uint64_t ls2 = 0;
 #pragma unroll
   for (uint32_t i = 0; i < kPer; ++i) {
-    c[i] = cnt[t * kPer + i];
+    c[i] = t * kPer + i < nb ? cnt[t * kPer + i] : 0u;
     ls += c[i];
     ls2 += uint64_t(c[i]) * c[i];
     mx = max(mx, c[i]);
@@ -409,13 +414,15 @@ __device__ void scan_buckets(const uint32_t* cnt, uint32_t* gst, uint32_t* soff,
   uint64_t run2 = we2 + inc2 - ls2;
 #pragma unroll
   for (uint32_t i = 0; i < kPer; ++i) {
-    gst[t * kPer + i] = run;
-    soff[t * kPer + i] = uint32_t(run2 < 0xFFFFFFFFull ? run2 : 0xFFFFFFFFull);
+    if (t * kPer + i < nb) {
+      gst[t * kPer + i] = run;
+      soff[t * kPer + i] = uint32_t(run2 < 0xFFFFFFFFull ? run2 : 0xFFFFFFFFull);
+    }
     run += c[i];
     run2 += uint64_t(c[i]) * c[i];
   }
-  if (t == kPartThreads - 1) {
-    gst[kB] = run;
+  if (t == kPartThreads - 1) {  // past every bucket: run = keys, run2 = sum s^2
+    gst[nb] = run;
     ctl.Spart = run2;
   }
   __syncthreads();
@@ -426,7 +433,7 @@ __device__ __noinline__ void count_global(const PassDev& p, const MapRegs& M, ui
                                           uint64_t e1, uint32_t* cnt) {
   for (uint64_t e = e0 + threadIdx.x; e < e1; e += kPartThreads) {
     const uint64_t k = p.stage_key[e];
-    atomicAdd(cnt + (reduce32(hash32(M.c1, k), M.n) - b0), 1u);
+    atomicAdd(cnt + (reduce32(hash32(M.c1, k), M.nb) - b0), 1u);
   }
 }
 
@@ -593,52 +600,97 @@ __device__ void place_thread(const PassDev& p, const uint64_t* k, const uint64_t
   }
 }
 
-// make_2 + placement for a bucket of kThreadSearchMax < s <= 32 keys by one
-// warp: lane x holds key x, a collision is two lanes with the same slot
-// (__match_any_sync).  Returns the attempt (or kSearchDup / kSearchNext).
+// make_2 + placement for up to 32 / G buckets of 2 <= s <= G keys by one warp
+// (G = 2^cls lanes per bucket, 2 <= G <= 32).  Lane x of segment q holds key
+// x of bucket list[q]; every segment tries attempts 0, 1, 2, ... in step and
+// keeps its first attempt without a collision (two of its lanes on one slot,
+// found with one __match_any_sync over (segment, slot) tags for the whole
+// warp), as the sequential make_2.  Statistics go to *amax / *asum (lane 0
+// of each segment).
 template <int PW>
-__device__ int search_place_warp(const PassDev& p, const uint64_t* k, const uint64_t* gpay, uint32_t g0,
-                                 uint32_t s, uint64_t seed, uint32_t round, uint32_t b, uint16_t* owner,
-                                 uint32_t so, uint64_t slot0, bool owner_mode) {
-  const uint32_t lane = lane_id(), m = s * s;
-  const bool mine = lane < s;
-  const uint64_t key = mine ? k[lane] : 0;
-  for (uint32_t a = 0; a < p.cfg.attempt_cap; ++a) {
-    if (a == kDupCheckAttempt) {
-      const uint32_t same = __match_any_sync(0xFFFFFFFFu, mine ? key : ~0ull);
-      bool eq = false, dup = false;
-      if (mine && __popc(same) > 1) {
-        eq = true;
-        for (uint32_t lower = same & lanemask_lt(); lower; lower &= lower - 1)  // every pair, as the oracle
-          dup |= same_member<PW>(p, gpay, g0 + uint32_t(__ffs(lower) - 1), g0 + lane);
-      }
-      if (__any_sync(0xFFFFFFFFu, dup)) return kSearchDup;
-      if (__any_sync(0xFFFFFFFFu, eq)) return kSearchNext;
-    }
-    const HashConsts c = derive(seed, round, b, a);
-    const uint32_t jj = mine ? reduce32(hash32(c, key), m) : 0xFFFFFFFFu - lane;
-    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, jj);
-    const bool col = __any_sync(0xFFFFFFFFu, mine && __popc(peers) > 1);
-    if (a < p.cfg.reject || col) continue;
-    // place: members, then the filler in every other slot of the range
-    const uint32_t jmin = __reduce_min_sync(0xFFFFFFFFu, mine ? jj : 0xFFFFFFFFu);
-    const uint32_t xmin = __ffs(__ballot_sync(0xFFFFFFFFu, mine && jj == jmin)) - 1;
-    if (owner_mode) {
-      if (mine) owner[so + jj] = uint16_t(g0 + lane);
-      __syncwarp();
-      for (uint32_t t = lane; t < m; t += 32)
-        if (owner[so + t] == kOwnerEmpty) owner[so + t] = uint16_t(kOwnerFill | (g0 + xmin));
-    } else {
-      for (uint32_t t = lane; t < m; t += 32) write_slot<PW>(p, slot0 + t, k[xmin], gpay + PW * (g0 + xmin), true);
-      __syncwarp();
-      if (mine) write_slot<PW>(p, slot0 + jj, key, gpay + PW * (g0 + lane), false);
-    }
-    return int(a);
+__device__ void search_place_seg(const PassDev& p, const uint64_t* gkey, const uint64_t* gpay,
+                                 const uint32_t* gst, const uint32_t* soff, const uint16_t* list,
+                                 uint32_t cnt, uint32_t cls, uint64_t seed, uint32_t round, uint32_t b0,
+                                 uint16_t* owner, uint64_t slot_part, bool owner_mode, uint32_t j,
+                                 PartCtl& ctl, uint16_t* att, uint32_t* amax, uint64_t* asum) {
+  const uint32_t lane = lane_id(), G = 1u << cls;
+  const uint32_t q = lane >> cls, x = lane & (G - 1u);
+  const uint32_t segmask = G == 32 ? 0xFFFFFFFFu : ((1u << G) - 1u) << (q * G);
+  const bool segv = q < cnt;
+  uint32_t lb = 0, g0 = 0, s = 0;
+  if (segv) {
+    lb = list[q];
+    g0 = gst[lb];
+    s = gst[lb + 1] - g0;
   }
-  return kSearchNext;
+  const bool mine = segv && x < s;
+  const uint64_t key = mine ? gkey[g0 + x] : 0ull;
+  const uint32_t m = s * s;
+  bool done = !segv;
+  int result = kSearchNext;
+  uint32_t myj = 0;
+  for (uint32_t a = 0; a < p.cfg.attempt_cap; ++a) {
+    if (__all_sync(0xFFFFFFFFu, done)) break;
+    if (a == kDupCheckAttempt) {
+      const uint32_t members = __ballot_sync(0xFFFFFFFFu, mine && !done);
+      const uint32_t same = __match_any_sync(0xFFFFFFFFu, key) & members & segmask;
+      bool eq = false, dup = false;
+      if (mine && !done && __popc(same) > 1) {
+        eq = true;
+        for (uint32_t lower = same & lanemask_lt(); lower; lower &= lower - 1)  // every equal pair
+          dup |= same_member<PW>(p, gpay, g0 + (uint32_t(__ffs(lower) - 1) - q * G), g0 + x);
+      }
+      const uint32_t eqm = __ballot_sync(0xFFFFFFFFu, eq), dupm = __ballot_sync(0xFFFFFFFFu, dup);
+      if (!done && (eqm & segmask)) {
+        result = (dupm & segmask) ? kSearchDup : kSearchNext;
+        done = true;
+      }
+    }
+    const bool live = mine && !done;
+    uint32_t jj = 0;
+    if (live) jj = reduce32(hash32(derive(seed, round, b0 + lb, a), key), m);
+    // (segment, slot) tag; idle lanes carry distinct values above every tag
+    const uint32_t tag = live ? ((q << 16) | jj) : 0xFFFFFFFFu - lane;
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, tag);
+    const uint32_t colm = __ballot_sync(0xFFFFFFFFu, live && __popc(peers) > 1);
+    if (!done && a >= p.cfg.reject && !(colm & segmask)) {
+      done = true;
+      result = int(a);
+      myj = jj;
+    }
+  }
+  // placement: members, then the filler (lowest occupied slot, value -1)
+  const bool ok = segv && result >= 0;
+  uint32_t v = (mine && ok) ? ((myj << 5) | x) : 0xFFFFFFFFu;
+  for (uint32_t d = G >> 1; d > 0; d >>= 1) v = min(v, __shfl_xor_sync(0xFFFFFFFFu, v, d));
+  const uint32_t xmin = v & 31u;
+  const uint32_t so = segv ? soff[lb] : 0u;
+  if (owner_mode) {
+    if (mine && ok) owner[so + myj] = uint16_t(g0 + x);
+    __syncwarp();
+    if (ok)
+      for (uint32_t t = x; t < m; t += G)
+        if (owner[so + t] == kOwnerEmpty) owner[so + t] = uint16_t(kOwnerFill | (g0 + xmin));
+  } else {
+    if (ok)
+      for (uint32_t t = x; t < m; t += G)
+        write_slot<PW>(p, slot_part + so + t, gkey[g0 + xmin], gpay + PW * (g0 + xmin), true);
+    __syncwarp();
+    if (mine && ok) write_slot<PW>(p, slot_part + so + myj, key, gpay + PW * (g0 + x), false);
+  }
+  if (segv && x == 0) {
+    if (result >= 0) {
+      att[lb] = uint16_t(result);
+      *amax = max(*amax, uint32_t(result));
+      *asum += uint64_t(result);
+    } else {
+      atomicExch(result == kSearchDup ? &p.status[j].dup : &p.status[j].next_round, 1u);
+      ctl.failed = 1;
+    }
+  }
 }
 
-// make_2 + placement for a bucket larger than kWarpSearchMax, by the CTA.
+// make_2 + placement for a bucket of more than 32 keys, by the CTA.
 template <int PW>
 __device__ __noinline__ void search_place_cta(const PassDev& p, const uint64_t* k, const uint64_t* gpay,
                                               uint32_t g0, uint32_t s, uint64_t seed, uint32_t round,
@@ -718,20 +770,33 @@ __device__ __noinline__ void search_place_cta(const PassDev& p, const uint64_t* 
   __syncthreads();
 }
 
+// Search classes of a bucket of s >= 2 keys: 0 = one thread (s <= thr), 1..5 =
+// a segment of 2^cls lanes (s <= 32), 6 = the whole CTA.
+constexpr uint32_t kClasses = 7;
+__device__ __forceinline__ uint32_t search_class(uint32_t s, uint32_t thr) {
+  if (s <= thr) return 0;
+  if (s > 32) return 6;
+  return 32u - uint32_t(__clz(int(s - 1)));  // ceil(log2 s)
+}
+
 // Level-two search (make_2) of every bucket of a grouped partition, then the
 // placement of its keys: slot image in shared memory (owner mode) or direct
-// writes.  Buckets above kThreadSearchMax keys are done by the whole CTA.
+// writes.  Empty and single-key buckets need no search (attempt 0); the
+// others are listed by class (counted, then placed, one shared atomic per
+// warp and class): small buckets are searched by single threads from the
+// low warps, mid-size ones in packed warp segments from the high warps (no
+// barrier between the two), buckets above 32 keys by the whole CTA.
 template <int PW>
 __device__ void search_partition(const PassDev& p, const MapRegs& M, uint32_t j, uint32_t b0,
                                  uint32_t nb, uint64_t slot_part, bool owner_mode,
                                  const uint64_t* gkey, const uint64_t* gpay, uint16_t* owner,
                                  const uint32_t* gst, const uint32_t* soff, uint16_t* att,
                                  uint16_t* work, PartCtl& ctl) {
-  // empty and single-key buckets need no search (attempt 0); the others are
-  // compacted into a worklist so that searching lanes sit side by side
-  // (one shared atomic per warp, not per bucket)
-  for (uint32_t lb0 = threadIdx.x & ~31u; lb0 < kB; lb0 += kPartThreads) {
-    const uint32_t lb = lb0 + lane_id();
+  const uint32_t thr = p.cfg.thread_max;
+  const uint32_t lane = lane_id();
+  // pass 1: singletons placed, classes counted
+  for (uint32_t lb0 = threadIdx.x & ~31u; lb0 < nb; lb0 += kPartThreads) {
+    const uint32_t lb = lb0 + lane;
     uint32_t g0 = 0, s = 0;
     if (lb < nb) {
       g0 = gst[lb];
@@ -742,21 +807,39 @@ __device__ void search_partition(const PassDev& p, const MapRegs& M, uint32_t j,
         else write_slot<PW>(p, slot_part + soff[lb], gkey[g0], gpay + PW * g0, false);
       }
     }
-    const bool want = lb < nb && s > 1 && s <= kThreadSearchMax;
-    const uint32_t m = __ballot_sync(0xFFFFFFFFu, want);
+    const uint32_t c = (lb < nb && s > 1) ? search_class(s, thr) : kClasses;
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, c);
+    if (c < kClasses && lane == uint32_t(__ffs(peers) - 1)) atomicAdd(&ctl.ccnt[c], uint32_t(__popc(peers)));
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t run = 0;
+    for (uint32_t c = 0; c < kClasses; ++c) {
+      ctl.cbase[c] = run;
+      ctl.ccur[c] = run;
+      run += ctl.ccnt[c];
+    }
+  }
+  __syncthreads();
+  // pass 2: the class lists
+  for (uint32_t lb0 = threadIdx.x & ~31u; lb0 < nb; lb0 += kPartThreads) {
+    const uint32_t lb = lb0 + lane;
+    uint32_t s = 0;
+    if (lb < nb) s = gst[lb + 1] - gst[lb];
+    const uint32_t c = (lb < nb && s > 1) ? search_class(s, thr) : kClasses;
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, c);
+    const uint32_t leader = uint32_t(__ffs(peers) - 1);
     uint32_t base = 0;
-    if (lane_id() == 0 && m) base = atomicAdd(&ctl.nwork, uint32_t(__popc(m)));
-    base = __shfl_sync(0xFFFFFFFFu, base, 0);
-    if (want) work[base + __popc(m & lanemask_lt())] = uint16_t(lb);
-    // larger buckets go to the end of the worklist (warp or CTA searches)
-    const bool big = lb < nb && s > kThreadSearchMax;
-    if (big) work[kB - 1 - atomicAdd(&ctl.nbig, 1u)] = uint16_t(lb);
+    if (c < kClasses && lane == leader) base = atomicAdd(&ctl.ccur[c], uint32_t(__popc(peers)));
+    base = __shfl_sync(0xFFFFFFFFu, base, leader);
+    if (c < kClasses) work[base + __popc(peers & lanemask_lt())] = uint16_t(lb);
   }
   __syncthreads();
   uint32_t my_max = 0;
   uint64_t my_sum = 0;
-  const uint32_t nwork = ctl.nwork;
-  for (uint32_t w = threadIdx.x; w < nwork; w += kPartThreads) {
+  // single-thread searches, from thread 0 up
+  const uint32_t n0 = ctl.ccnt[0];
+  for (uint32_t w = threadIdx.x; w < n0; w += kPartThreads) {
     const uint32_t lb = work[w];
     const uint32_t g0 = gst[lb], s = gst[lb + 1] - g0;
     HashConsts c;
@@ -772,47 +855,41 @@ __device__ void search_partition(const PassDev& p, const MapRegs& M, uint32_t j,
       ctl.failed = 1;
     }
   }
+  // warp segments, from the last warp down: chunk k of class c holds 32 / 2^c buckets
+  {
+    uint32_t chunks[6], total = 0;
+#pragma unroll
+    for (uint32_t c = 1; c <= 5; ++c) {
+      const uint32_t per = 32u >> c;
+      chunks[c] = (ctl.ccnt[c] + per - 1) / per;
+      total += chunks[c];
+    }
+    constexpr uint32_t kWarps = kPartThreads / 32;
+    for (uint32_t k = kWarps - 1 - (threadIdx.x >> 5); k < total; k += kWarps) {
+      uint32_t c = 1, r = k;
+      while (r >= chunks[c]) r -= chunks[c++];
+      const uint32_t per = 32u >> c;
+      const uint32_t first = r * per;
+      const uint32_t cnt = min(per, ctl.ccnt[c] - first);
+      search_place_seg<PW>(p, gkey, gpay, gst, soff, work + ctl.cbase[c] + first, cnt, c, M.seed, M.round, b0,
+                           owner, slot_part, owner_mode, j, ctl, att, &my_max, &my_sum);
+    }
+  }
   // statistics: one shared atomic per warp
   my_max = __reduce_max_sync(0xFFFFFFFFu, my_max);
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) my_sum += __shfl_xor_sync(0xFFFFFFFFu, my_sum, d);
-  if (lane_id() == 0) {
+  if (lane == 0) {
     if (my_max) atomicMax(&ctl.maxatt, my_max);
     if (my_sum) atomicAdd(reinterpret_cast<unsigned long long*>(&ctl.attsum), my_sum);
   }
   __syncthreads();
-  if (ctl.nbig) {
-    const uint32_t nbig = ctl.nbig;
-    // 8 < s <= 32: one warp per bucket
-    uint32_t wmax = 0;
-    uint64_t wsum = 0;
-    for (uint32_t i = threadIdx.x >> 5; i < nbig; i += kPartThreads / 32) {
-      const uint32_t lb = work[kB - 1 - i];
+  // s > 32 (adversarial inputs, or many keys per bucket): the whole CTA, one bucket at a time
+  const uint32_t n6 = ctl.ccnt[6];
+  if (n6) {
+    for (uint32_t i = 0; i < n6; ++i) {
+      const uint32_t lb = work[ctl.cbase[6] + i];
       const uint32_t g0 = gst[lb], s = gst[lb + 1] - g0;
-      if (s > kWarpSearchMax) continue;
-      const int a = search_place_warp<PW>(p, gkey + g0, gpay, g0, s, M.seed, M.round, b0 + lb, owner, soff[lb],
-                                          slot_part + soff[lb], owner_mode);
-      if (lane_id() == 0) {
-        if (a >= 0) {
-          att[lb] = uint16_t(a);
-          wmax = max(wmax, uint32_t(a));
-          wsum += uint64_t(a);
-        } else {
-          atomicExch(a == kSearchDup ? &p.status[j].dup : &p.status[j].next_round, 1u);
-          ctl.failed = 1;
-        }
-      }
-    }
-    if (lane_id() == 0) {
-      if (wmax) atomicMax(&ctl.maxatt, wmax);
-      if (wsum) atomicAdd(reinterpret_cast<unsigned long long*>(&ctl.attsum), wsum);
-    }
-    __syncthreads();
-    // s > 32 (adversarial inputs only): the whole CTA, one bucket at a time
-    for (uint32_t i = 0; i < nbig; ++i) {
-      const uint32_t lb = work[kB - 1 - i];
-      const uint32_t g0 = gst[lb], s = gst[lb + 1] - g0;
-      if (s <= kWarpSearchMax) continue;
       search_place_cta<PW>(p, gkey + g0, gpay, g0, s, M.seed, M.round, b0 + lb, owner, soff[lb],
                            slot_part + soff[lb], owner_mode, j, ctl, att + lb);
     }
@@ -892,7 +969,7 @@ __global__ void __launch_bounds__(kPartThreads, PW == 1 ? 2 : 1) k_part_build(Pa
     ++iter;
     const uint64_t e0 = p.part_start[gp], e1 = p.part_start[gp + 1];
     const uint32_t ne = uint32_t(e1 - e0 < 0xFFFFFFFFull ? e1 - e0 : 0xFFFFFFFFull);
-    for (uint32_t i = t; i < kB; i += kPartThreads) cnt[i] = 0;
+    for (uint32_t i = t; i < (1u << p.logB); i += kPartThreads) cnt[i] = 0;
     if (issued) {  // bounded wait for the staged copy
       uint32_t polls = 0;
       while (!mbar_try_wait(&bar, parity)) {
@@ -911,9 +988,11 @@ __global__ void __launch_bounds__(kPartThreads, PW == 1 ? 2 : 1) k_part_build(Pa
     if (t == 0) {  // every reader of last iteration's values passed the barrier above
       ctl.maxs = ctl.maxatt = ctl.nonempty = ctl.nbig = ctl.failed = ctl.nwork = 0;
       ctl.attsum = 0;
+      for (uint32_t c = 0; c < 8; ++c) ctl.ccnt[c] = 0;
     }
-    const uint32_t b0 = (gp - M.part_begin) << kLogB;
-    const uint32_t nb = min(kB, M.n - b0);
+    // M (written by thread 32 above) is visible past the barrier
+    const uint32_t b0 = (gp - M.part_begin) << p.logB;
+    const uint32_t nb = min(1u << p.logB, M.nb - b0);  // buckets of this partition
     const bool overflow = ne > kCap;
     const uint32_t shift = uint32_t(e0 & 1ull);  // raw key index of element e0
     uint16_t lbr[kPerThread], rk[kPerThread];
@@ -925,7 +1004,7 @@ __global__ void __launch_bounds__(kPartThreads, PW == 1 ? 2 : 1) k_part_build(Pa
         const uint32_t i = t + u * kPartThreads;
         if (i < ne) {
           const uint64_t k = raw_key[shift + i];
-          const uint32_t lb = reduce32(hash32(M.c1, k), M.n) - b0;
+          const uint32_t lb = reduce32(hash32(M.c1, k), M.nb) - b0;
           lbr[u] = uint16_t(lb);
           rk[u] = uint16_t(atomicAdd(cnt + lb, 1u));
         }
@@ -934,7 +1013,7 @@ __global__ void __launch_bounds__(kPartThreads, PW == 1 ? 2 : 1) k_part_build(Pa
       count_global(p, M, b0, e0, e1, cnt);
     }
     __syncthreads();
-    scan_buckets(cnt, gst, soff, ctl);
+    scan_buckets(cnt, gst, soff, ctl, nb);
     const uint64_t Sp = ctl.Spart;
     const bool owner_mode = Sp <= kOwnerCap;
     // The slot prefix of this partition (look-back across partitions) is
@@ -1018,30 +1097,31 @@ __global__ void __launch_bounds__(kPartThreads, 1) k_part_overflow(PassDev p) {
   const uint32_t gp = p.ovf_list[blockIdx.x];
   const uint32_t j = p.m == 1 ? 0u : upper_seg(p.part_seg, p.m, gp);
   const MapRegs M = load_map(p, j);
-  const uint32_t b0 = (gp - M.part_begin) << kLogB;
-  const uint32_t nb = min(kB, M.n - b0);
+  const uint32_t b0 = (gp - M.part_begin) << p.logB;
+  const uint32_t nb = min(1u << p.logB, M.nb - b0);
   const uint64_t e0 = p.part_start[gp], e1 = p.part_start[gp + 1];
   const uint64_t excl = p.ovf_excl[blockIdx.x];
   uint64_t* gkey = p.ovf_key + e0;
   uint64_t* gpay = p.ovf_pay + PW * e0;
-  for (uint32_t i = t; i < kB; i += kPartThreads) cnt[i] = 0;
+  for (uint32_t i = t; i < nb; i += kPartThreads) cnt[i] = 0;
   if (t == 0) {
     ctl.maxs = ctl.maxatt = ctl.nonempty = ctl.nbig = ctl.failed = ctl.nwork = 0;
     ctl.attsum = 0;
+    for (uint32_t c = 0; c < 8; ++c) ctl.ccnt[c] = 0;
   }
   __syncthreads();
   count_global(p, M, b0, e0, e1, cnt);
   __syncthreads();
-  scan_buckets(cnt, gst, soff, ctl);
+  scan_buckets(cnt, gst, soff, ctl, nb);
   const uint64_t Sp = ctl.Spart;
   const bool owner_mode = Sp <= kOwnerCap;
-  for (uint32_t i = t; i < kB; i += kPartThreads) cnt[i] = gst[i];
+  for (uint32_t i = t; i < nb; i += kPartThreads) cnt[i] = gst[i];
   if (owner_mode)
     for (uint32_t q = t; q < uint32_t(Sp); q += kPartThreads) owner[q] = kOwnerEmpty;
   __syncthreads();
   for (uint64_t e = e0 + t; e < e1; e += kPartThreads) {
     const uint64_t k = p.stage_key[e];
-    const uint32_t lb = reduce32(hash32(M.c1, k), M.n) - b0;
+    const uint32_t lb = reduce32(hash32(M.c1, k), M.nb) - b0;
     const uint32_t pos = atomicAdd(cnt + lb, 1u);
     gkey[pos] = k;
 #pragma unroll

@@ -10,16 +10,30 @@ struct fks_map;  // handle type of the C ABI (fks_api.cu)
 
 namespace fks {
 
-// Level-one buckets are processed in partitions of kB consecutive buckets.
-// A partition's keys (about kB of them, since there are n buckets for n
-// keys) are grouped, searched and placed inside one CTA's shared memory.
+// Level-one buckets are processed in partitions of consecutive buckets,
+// at most kB of them.  A partition's keys are grouped, searched and placed
+// inside one CTA's shared memory.  With one bucket per key (the paper's
+// construction) a partition is kB buckets, about kB keys and 2 kB slots.
 constexpr int kLogB = 10;
 constexpr uint32_t kB = 1u << kLogB;
 constexpr uint32_t kCap = 2048;        // keys of a partition held in shared memory
-constexpr uint32_t kOwnerCap = 4096;   // slots of a partition staged in shared memory
+constexpr uint32_t kOwnerCap = 8192;   // slots of a partition staged in shared memory
+
+// Buckets per partition (log2) for lambda keys per bucket: kB / lambda, so
+// that a partition holds about kB keys whatever lambda.  Its slot image,
+// about (1 + lambda) kB slots, is staged in shared memory when it fits
+// kOwnerCap (lambda <= 4); larger images are written straight to global
+// memory, bucket range by bucket range (coalesced for the warp-searched
+// buckets such maps consist of).
+__host__ __device__ constexpr uint32_t part_log_buckets(uint32_t lambda) {
+  return lambda <= 1 ? 10u : lambda == 2 ? 9u : lambda == 4 ? 8u : lambda == 8 ? 7u : 6u;
+}
+// Level-one buckets of an n-key map with lambda keys per bucket.
+__host__ __device__ constexpr uint64_t level1_buckets(uint64_t n, uint32_t lambda) {
+  return (n + lambda - 1) / lambda;
+}
 constexpr int kPartThreads = 512;      // threads of a partition CTA
-constexpr uint32_t kThreadSearchMax = 8;   // buckets up to this size: one thread each
-constexpr uint32_t kWarpSearchMax = 32;   // up to this size: one warp (lane = key); larger: the CTA
+constexpr uint32_t kThreadSearchMax = 8;  // largest bucket a single thread can search (64-bit bitmap)
 constexpr uint16_t kOwnerEmpty = 0xFFFF;
 constexpr uint16_t kOwnerFill = 0x8000;
 
@@ -35,7 +49,8 @@ struct MapDev {
   uint64_t seed;
   uint64_t fpb;         // fingerprint base of this round (string maps)
   HashConsts c1;        // level-one constants of this round
-  uint32_t n;           // keys = level-one buckets
+  uint32_t n;           // keys
+  uint32_t nb;          // level-one buckets (= descriptors)
   uint32_t round;
   uint32_t slot_cap;    // bound_factor * n
   uint32_t part_begin;  // first partition (pass numbering)
@@ -61,6 +76,7 @@ struct BuildCfg {
   uint32_t reject;       // test hook: attempts below this count as failed
   uint32_t spin_limit;   // polls of a look-back wait before giving up
   uint32_t hold_first;   // test hook: partition 0 never publishes (forces a timeout)
+  uint32_t thread_max;   // buckets of 2 .. thread_max keys are searched by one thread each
 };
 
 // Everything a pass's kernels read; passed by value.
@@ -71,6 +87,7 @@ struct PassDev {
   const uint32_t* part_seg;   // [m+1] partition offsets
   uint32_t m;
   uint32_t P;                 // partitions
+  uint32_t logB;              // log2 of the buckets per partition
   uint64_t total;             // pass elements
   // inputs
   const uint64_t* hkeys;      // u64 keys, or fingerprints of string keys (input numbering)
@@ -152,7 +169,7 @@ struct LookupMap {
   HashConsts c1;
   uint64_t seed;
   uint64_t fpb;
-  uint32_t n;
+  uint32_t nb;             // level-one buckets
   uint32_t round;
 };
 cudaError_t launch_lookup_u64(const LookupMap& M, const uint64_t* q, uint64_t nq, void* out,

@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(kLookupThreads) k_lookup_u64(LookupMap M,
     uint64_t d[kQ];
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
-      b[i] = reduce32(hash32(M.c1, k[i]), M.n);
+      b[i] = reduce32(hash32(M.c1, k[i]), M.nb);
       d[i] = ld_na_u64(M.desc + b[i], keep);
     }
     ulonglong2 sl[kQ];
@@ -150,7 +150,7 @@ __device__ __forceinline__ bool lookup_one_bytes(const LookupMap& M, const uint8
   uint64_t h = len;
   const uint32_t words = (len + 3u) >> 2;
   for (uint32_t t = 0; t < words; ++t) h = addmod61(mulmod61(h, M.fpb), str_word(s, len, t));
-  const uint32_t b = reduce32(hash32(M.c1, h), M.n);
+  const uint32_t b = reduce32(hash32(M.c1, h), M.nb);
   const uint64_t d = ld_na_u64(M.desc + b, keep);
   const uint32_t sz = desc_s(d);
   if (!sz) return false;
@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(kLookupThreads) k_lookup_batched(
         d[i] = 0;
         b[i] = 0;
         if (id[i] < m) {
-          b[i] = reduce32(hash32(maps[id[i]].c1, k[i]), maps[id[i]].n);
+          b[i] = reduce32(hash32(maps[id[i]].c1, k[i]), maps[id[i]].nb);
           d[i] = ld_na_u64(maps[id[i]].desc + b[i], keep);
         }
       }
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(kLookupThreads) k_lookup_requests(const Lookup
     bool hit = false;
     if (!R.strings) {
       const uint64_t k = __ldcs(R.q + local);
-      const uint32_t bk = reduce32(hash32(R.M.c1, k), R.M.n);
+      const uint32_t bk = reduce32(hash32(R.M.c1, k), R.M.nb);
       const uint64_t d = ld_na_u64(R.M.desc + bk, keep);
       const uint32_t s = desc_s(d);
       if (s) {

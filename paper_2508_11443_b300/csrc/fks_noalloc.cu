@@ -123,6 +123,10 @@ extern "C" fks_status fks_build_u64_noalloc(const uint64_t* keys, const void* va
     if (opts->spin_limit) spin = opts->spin_limit;
     if (attempt_cap > 4095 || round_cap > 65535 || bound < 1 || bound > 4)
       return noalloc_fail(FKS_ERR_INVALID_ARG, "fks_build_u64_noalloc: bad options");
+    // the scratch array is sized for one level-one bucket per key
+    if (opts->struct_size >= offsetof(fks_build_opts, keys_per_bucket) + sizeof(uint32_t) &&
+        opts->keys_per_bucket > 1)
+      return noalloc_fail(FKS_ERR_INVALID_ARG, "fks_build_u64_noalloc: keys_per_bucket must be 1");
   }
   if (slot_capacity < uint64_t(bound) * n)
     return noalloc_fail(FKS_ERR_INVALID_ARG,
@@ -158,6 +162,7 @@ extern "C" fks_status fks_build_u64_noalloc(const uint64_t* keys, const void* va
   p.m = 1;
   p.P = P;
   p.total = n;
+  p.logB = kLogB;
   p.hkeys = keys;
   p.vals = vals;
   p.vals_i64 = val_type == FKS_VAL_I64;
@@ -167,6 +172,7 @@ extern "C" fks_status fks_build_u64_noalloc(const uint64_t* keys, const void* va
   p.cfg.reject = reject;
   p.cfg.spin_limit = spin;
   p.cfg.hold_first = 0;
+  p.cfg.thread_max = 3;
 
   // control words live on the host stack (pageable copies; nothing allocated)
   const uint64_t h_pseg[2] = {0, n};
@@ -188,6 +194,7 @@ extern "C" fks_status fks_build_u64_noalloc(const uint64_t* keys, const void* va
     M.round = r;
     M.c1 = derive(seed, r, kTagLevel1, 0);
     M.n = uint32_t(n);
+    M.nb = uint32_t(n);
     M.slot_cap = uint32_t(uint64_t(bound) * n);
     NOALLOC_CUDA(cudaMemcpyAsync(d_maps, &M, sizeof(M), cudaMemcpyHostToDevice, s));
     NOALLOC_CUDA(cudaMemsetAsync(d_stat, 0, sizeof(MapStatus), s));
@@ -218,6 +225,8 @@ extern "C" fks_status fks_build_u64_noalloc(const uint64_t* keys, const void* va
       h_info->val_type = val_type;
       h_info->overflow_partitions = h_stat.overflow;
       h_info->nonempty_buckets = h_stat.nonempty;
+      h_info->buckets = n;
+      h_info->keys_per_bucket = 1;
     }
     return FKS_OK;
   }

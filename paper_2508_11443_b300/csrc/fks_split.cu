@@ -3,7 +3,7 @@
 //
 // The paper groups keys by their level-one bucket with Hist + Groupby (Sec.
 // 2.3-2.5).  Here keys are first brought into contiguous partition ranges
-// (a partition = 1024 consecutive buckets), each then handled by one CTA in
+// (a partition = up to 1024 consecutive buckets), each then handled by one CTA in
 // k_part_build.  A single scatter with one atomic per key into ~n/1024
 // partitions is bound by the L2 atomic rate; two levels of at most a few
 // hundred bins each make every write part of a contiguous run and use no
@@ -57,7 +57,7 @@ __device__ __forceinline__ Elem<kStr> load_elem(const PassDev& p, const uint64_t
   const uint64_t in = M.key_begin + (e - M.pass_begin);
   Elem<kStr> x;
   x.key = __ldcs(reinterpret_cast<const unsigned long long*>(p.hkeys) + in);
-  x.gp = M.part_begin + (reduce32(hash32(M.c1, x.key), M.n) >> kLogB);
+  x.gp = M.part_begin + (reduce32(hash32(M.c1, x.key), M.nb) >> p.logB);
   const int64_t v = p.vals_i64 ? __ldcs(static_cast<const long long*>(p.vals) + in)
                                : int64_t(__ldcs(static_cast<const int*>(p.vals) + in));
   if (!kStr) {
@@ -77,7 +77,7 @@ __device__ __forceinline__ uint32_t gp_only(const PassDev& p, const uint64_t* se
   const uint32_t j = p.m == 1 ? 0u : seg_of(seg, p.m, e);
   const MapDev& M = p.maps[j];
   const uint64_t k = __ldcs(reinterpret_cast<const unsigned long long*>(p.hkeys) + M.key_begin + (e - M.pass_begin));
-  return M.part_begin + (reduce32(hash32(M.c1, k), M.n) >> kLogB);
+  return M.part_begin + (reduce32(hash32(M.c1, k), M.nb) >> p.logB);
 }
 
 // Level-B tile t -> (level-A bin, first element, end element).

@@ -38,7 +38,8 @@ class FksError(RuntimeError):
 class fks_build_opts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_size_t), ("bound_factor", ctypes.c_uint32),
                 ("attempt_cap", ctypes.c_uint32), ("round_cap", ctypes.c_uint32),
-                ("reject_attempts", ctypes.c_uint32), ("spin_limit", ctypes.c_uint32)]
+                ("reject_attempts", ctypes.c_uint32), ("spin_limit", ctypes.c_uint32),
+                ("keys_per_bucket", ctypes.c_uint32)]
 
 
 class fks_map_info_t(ctypes.Structure):
@@ -48,7 +49,8 @@ class fks_map_info_t(ctypes.Structure):
                 ("round", ctypes.c_uint32), ("max_bucket", ctypes.c_uint32),
                 ("max_attempt", ctypes.c_uint32), ("key_kind", ctypes.c_uint32),
                 ("val_type", ctypes.c_uint32), ("overflow_partitions", ctypes.c_uint32),
-                ("nonempty_buckets", ctypes.c_uint64)]
+                ("nonempty_buckets", ctypes.c_uint64), ("buckets", ctypes.c_uint64),
+                ("keys_per_bucket", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class fks_build_profile(ctypes.Structure):
@@ -261,10 +263,10 @@ def fks_map_info(m: Map) -> fks_map_info_t:
 
 
 def fks_map_export(m: Map, stream=None):
-    """(desc uint64[n], slots uint64[S, 2 or 4], ctx uint8[] or None) on the host."""
+    """(desc uint64[buckets], slots uint64[S, 2 or 4], ctx uint8[] or None) on the host."""
     info = fks_map_info(m)
     words = 4 if info.key_kind == FKS_KEY_BYTES else 2
-    desc = np.empty(info.n, np.uint64)
+    desc = np.empty(info.buckets, np.uint64)
     slots = np.empty((info.slots, words), np.uint64)
     ctx = np.empty(max(info.context_bytes, 1), np.uint8) if info.key_kind == FKS_KEY_BYTES else None
     _check(lib().fks_map_export(m.handle, desc.ctypes.data_as(ctypes.c_void_p),

@@ -253,7 +253,7 @@ def test_invalid_arguments(F):
         F.fks_build_u64(u64(np.arange(5, dtype=np.uint64)), dev(np.zeros(5, np.float32)), 1)
     with pytest.raises(F.FksError):
         F.fks_build_u64(u64(np.arange(5, dtype=np.uint64)), dev(np.arange(5)), 1,
-                        F.make_opts(bound_factor=9))
+                        F.make_opts(bound_factor=65))
 
 
 def test_full_size_config2_bit_exact(F):
