@@ -81,6 +81,8 @@ def lib():
         L.or_l1_counts.argtypes = [vp, u64, u64, u64, u32, vp]
         L.or_fingerprints.restype = None
         L.or_fingerprints.argtypes = [vp, vp, u64, u64, u32, vp]
+        L.or_dedup.restype = u64
+        L.or_dedup.argtypes = [vp, vp, vp, u64, vp, u32, vp]
         L.or_binary_search.restype = ctypes.c_int64
         L.or_binary_search.argtypes = [vp, u64, u64]
         _lib = L
@@ -260,6 +262,33 @@ def fingerprints(ctx, offs, seed: int, round_: int) -> np.ndarray:
     out = np.zeros(offs.size - 1, np.uint64)
     lib().or_fingerprints(_p(ctx), _p(offs), offs.size - 1, seed & (2**64 - 1), round_, _p(out))
     return out
+
+
+def dedup_keep(keys=None, ctx=None, offs=None, seg=None) -> np.ndarray:
+    """from_array's first-occurrence rule: keep[e] = 1 iff no earlier element
+    of e's segment has an equal key (uint64 keys, or byte strings ctx/offs)."""
+    if keys is not None:
+        k = _c(keys, np.uint64)
+        u = k.size
+        kp, cp, op = _p(k), None, None
+    else:
+        cx = _c(ctx, np.uint8)
+        if cx.size == 0:
+            cx = np.zeros(1, np.uint8)
+        of = _c(offs, np.int64)
+        u = of.size - 1
+        kp, cp, op = None, _p(cx), _p(of)
+    keep = np.zeros(max(u, 1), np.uint8)
+    sg = None if seg is None else _c(seg, np.int64)
+    lib().or_dedup(kp, cp, op, u, None if sg is None else _p(sg), 0 if sg is None else sg.size - 1,
+                   _p(keep))
+    return keep[:u]
+
+
+def from_array_u64(keys, vals, seed: int, **opts) -> Map:
+    """from_array over uint64 keys: duplicates allowed, first occurrence wins."""
+    keep = dedup_keep(keys=keys).astype(bool)
+    return build_u64(np.asarray(keys, np.uint64)[keep], np.asarray(vals, np.int64)[keep], seed, **opts)
 
 
 def binary_search(sorted_keys, q: int) -> int:

@@ -447,6 +447,67 @@ int or_build_bytes(const uint8_t* ctx, const int64_t* offs, const int64_t* vals,
   return st;
 }
 
+/* from_array (Sec. 3.2): the constructor that accepts duplicate keys.  The
+ * paper leaves the surviving pair unspecified; reading: the first occurrence
+ * in input order wins.  keep[e] = 1 iff no earlier element of the same
+ * segment has an equal key (u64: equal words; strings: equal bytes).  seg
+ * holds m + 1 segment offsets (NULL: one segment).  Written as its
+ * definition: sort the indices by (segment, key, index) and keep the first
+ * index of every run of equal (segment, key). */
+static const uint64_t* g_dd_keys;
+static const uint8_t* g_dd_ctx;
+static const int64_t* g_dd_offs;
+static const uint32_t* g_dd_segid;
+static int or_cmp_dedup(const void* a, const void* b) {
+  uint64_t i = *(const uint64_t*)a, j = *(const uint64_t*)b;
+  if (g_dd_segid[i] != g_dd_segid[j]) return g_dd_segid[i] < g_dd_segid[j] ? -1 : 1;
+  int c = 0;
+  if (g_dd_keys) {
+    c = g_dd_keys[i] < g_dd_keys[j] ? -1 : g_dd_keys[i] > g_dd_keys[j];
+  } else {
+    int64_t li = g_dd_offs[i + 1] - g_dd_offs[i], lj = g_dd_offs[j + 1] - g_dd_offs[j];
+    if (li != lj) c = li < lj ? -1 : 1;
+    else c = memcmp(g_dd_ctx + g_dd_offs[i], g_dd_ctx + g_dd_offs[j], (size_t)li);
+  }
+  if (c) return c;
+  return i < j ? -1 : i > j;
+}
+
+static int or_same_key(uint64_t i, uint64_t j) {
+  if (g_dd_segid[i] != g_dd_segid[j]) return 0;
+  if (g_dd_keys) return g_dd_keys[i] == g_dd_keys[j];
+  int64_t li = g_dd_offs[i + 1] - g_dd_offs[i], lj = g_dd_offs[j + 1] - g_dd_offs[j];
+  return li == lj && memcmp(g_dd_ctx + g_dd_offs[i], g_dd_ctx + g_dd_offs[j], (size_t)li) == 0;
+}
+
+/* keys (u64) or ctx/offs (strings); returns the number of kept elements. */
+uint64_t or_dedup(const uint64_t* keys, const uint8_t* ctx, const int64_t* offs, uint64_t u,
+                  const int64_t* seg, uint32_t m, uint8_t* keep) {
+  uint64_t* idx = (uint64_t*)malloc((u ? u : 1) * sizeof(uint64_t));
+  uint32_t* segid = (uint32_t*)malloc((u ? u : 1) * sizeof(uint32_t));
+  for (uint64_t e = 0; e < u; ++e) idx[e] = e;
+  if (seg) {
+    for (uint32_t j = 0; j < m; ++j)
+      for (int64_t e = seg[j]; e < seg[j + 1]; ++e) segid[e] = j;
+  } else {
+    for (uint64_t e = 0; e < u; ++e) segid[e] = 0;
+  }
+  g_dd_keys = keys;
+  g_dd_ctx = ctx;
+  g_dd_offs = offs;
+  g_dd_segid = segid;
+  qsort(idx, u, sizeof(uint64_t), or_cmp_dedup);
+  uint64_t kept = 0;
+  for (uint64_t r = 0; r < u; ++r) {
+    int first = r == 0 || !or_same_key(idx[r - 1], idx[r]);
+    keep[idx[r]] = (uint8_t)first;
+    kept += (uint64_t)first;
+  }
+  free(idx);
+  free(segid);
+  return kept;
+}
+
 /* Lookup (Sec. 2.2 membership test; Sec. 3.2 lookup -> opt v).
  * nb = the map's level-one buckets (n for the paper's construction).
  * found[i] = 1 and out[i] = value for members, found[i] = 0 and

@@ -484,3 +484,57 @@ def test_bucket_variant_strings(lam):
     out, found = O.lookup_bytes(m, w.qctx, w.qoffs, absent=-3)
     assert np.array_equal(found, w.expect_found)
     assert np.array_equal(out, np.where(w.expect_found == 1, w.expect_vals, -3))
+
+
+# ------------------------------------------------------------------ from_array (deduplication)
+def _first_occurrence_dict(items, segs=None):
+    """Independent brute force: a Python set per segment, walked in input order."""
+    keep = []
+    seen = {}
+    for e, k in enumerate(items):
+        g = 0 if segs is None else segs[e]
+        key = (g, k)
+        keep.append(key not in seen)
+        seen.setdefault(key, e)
+    return np.array(keep, np.uint8)
+
+
+def test_dedup_u64_first_occurrence():
+    rng = np.random.default_rng(11)
+    for trial in range(50):
+        u = int(rng.integers(1, 400))
+        universe = int(rng.integers(1, 50))
+        keys = rng.integers(0, universe, u).astype(np.uint64) * np.uint64(0x9E3779B97F4A7C15)
+        keep = O.dedup_keep(keys=keys)
+        assert np.array_equal(keep, _first_occurrence_dict(keys.tolist()))
+
+
+def test_dedup_strings_and_segments():
+    rng = np.random.default_rng(12)
+    words = [b"", b"a", b"ab", b"abc", b"b", b"ba", b"abcd" * 5, b"x" * 70]
+    for trial in range(30):
+        u = int(rng.integers(1, 200))
+        pick = [words[i] for i in rng.integers(0, len(words), u)]
+        offs = np.concatenate([[0], np.cumsum([len(w) for w in pick])]).astype(np.int64)
+        ctx = np.frombuffer(b"".join(pick) + b"\0", np.uint8)[: offs[-1]]
+        m = int(rng.integers(1, 5))
+        cuts = np.sort(rng.choice(np.arange(1, u), size=min(m - 1, u - 1), replace=False)) if u > 1 else []
+        seg = np.concatenate([[0], cuts, [u]]).astype(np.int64)
+        segs = np.repeat(np.arange(seg.size - 1), np.diff(seg))
+        keep = O.dedup_keep(ctx=ctx, offs=offs, seg=seg)
+        assert np.array_equal(keep, _first_occurrence_dict(pick, segs.tolist()))
+
+
+def test_from_array_lookups_follow_first_occurrence():
+    rng = np.random.default_rng(13)
+    keys = rng.integers(0, 3000, 10000).astype(np.uint64)
+    vals = np.arange(10000, dtype=np.int64)
+    m = O.from_array_u64(keys, vals, seed=3)
+    assert m.status == O.OK and m.n == np.unique(keys).size
+    first = {}
+    for e, k in enumerate(keys.tolist()):
+        first.setdefault(k, e)
+    q = np.arange(3100, dtype=np.uint64)
+    out, found = O.lookup_u64(m, q)
+    for k, v, f in zip(q.tolist(), out.tolist(), found.tolist()):
+        assert f == (k in first) and v == first.get(k, -1)
