@@ -83,7 +83,13 @@ typedef struct {
  * level-one round passes the space bound with probability >= 1/2 as in the
  * paper's analysis.  bound_factor * n must stay below 2^32 (slot offsets
  * are 32-bit descriptor fields); larger builds return FKS_ERR_INVALID_ARG.
- * A struct_size that ends before keys_per_bucket is accepted (lambda 1). */
+ * A struct_size that ends before keys_per_bucket is accepted (lambda 1).
+ *
+ * dedup = 1 turns a build into the paper's from_array (Sec. 3.2): the input
+ * may hold equal keys (equal words, or equal byte strings), and the first
+ * occurrence in input order wins -- per map for fks_build_batched.  The map
+ * holds the distinct keys (fks_map_info: n).  The paper leaves the winner
+ * unspecified; with dedup = 0 (from_array_nodup) equal keys are an error. */
 typedef struct {
   size_t struct_size;        /* sizeof(fks_build_opts)                          */
   uint32_t bound_factor;     /* level-one redraw when sum s^2 > bound*n (2 (1 + lambda)) */
@@ -92,6 +98,7 @@ typedef struct {
   uint32_t reject_attempts;  /* TEST HOOK: attempts below this count as failed (0) */
   uint32_t spin_limit;       /* bound of every device wait, in polls (1<<20)     */
   uint32_t keys_per_bucket;  /* lambda: 1 (the paper), 2, 4, 8 or 16 (1)        */
+  uint32_t dedup;            /* 1: from_array -- duplicate keys allowed (0)     */
 } fks_build_opts;
 
 typedef struct {
@@ -221,7 +228,8 @@ fks_map_t fks_mapset_get(fks_mapset_t set, uint32_t j);
  * FKS_ERR_INVALID_ARG.
  *   keys, vals, val_type, n, seed, opts   as for fks_build_u64, with one
  *                  level-one bucket per key (keys_per_bucket other than 0
- *                  or 1 returns FKS_ERR_INVALID_ARG; bound_factor <= 4)
+ *                  or 1 returns FKS_ERR_INVALID_ARG; bound_factor <= 4) and
+ *                  distinct keys (dedup = 1 returns FKS_ERR_INVALID_ARG)
  *   desc_out       uint64[n] (device): the bucket descriptors
  *   slots_out      slot_capacity slots of 16 bytes (device), slot_capacity >=
  *                  bound_factor * n; the first info.slots slots are the table

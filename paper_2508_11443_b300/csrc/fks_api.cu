@@ -225,6 +225,7 @@ static LookupMap lookup_view(const fks_map& m) {
 struct Opts {
   uint32_t bound = 4, attempt_cap = 4095, round_cap = 32, reject = 0, spin = 1u << 20, hold = 0;
   uint32_t lambda = 1;  // keys per level-one bucket
+  uint32_t dedup = 0;   // from_array: first occurrence of equal keys wins
 };
 
 // Options of the older, shorter layout (without keys_per_bucket) are accepted.
@@ -233,6 +234,10 @@ static bool read_opts(const fks_build_opts* o, Opts* out) {
   if (o->struct_size < offsetof(fks_build_opts, spin_limit) + sizeof(uint32_t)) return false;
   if (o->struct_size >= offsetof(fks_build_opts, keys_per_bucket) + sizeof(uint32_t) && o->keys_per_bucket)
     out->lambda = o->keys_per_bucket;
+  if (o->struct_size >= offsetof(fks_build_opts, dedup) + sizeof(uint32_t)) {
+    if (o->dedup > 1) return false;
+    out->dedup = o->dedup;
+  }
   if (out->lambda != 1 && out->lambda != 2 && out->lambda != 4 && out->lambda != 8 && out->lambda != 16)
     return false;
   out->bound = 2 * (1 + out->lambda);  // E[sum s^2] < (1 + lambda) n: bound = twice that
@@ -624,6 +629,91 @@ static const char* status_name(fks_status s) {
   return "unknown status";
 }
 
+// ---------------------------------------------------------------- from_array
+// The deduplicated inputs of a build (kept pairs in input order) and the
+// block that holds them until the build has read them.
+struct DedupOut {
+  uint8_t* block = nullptr;
+  size_t bytes = 0;
+  BuildIn in{};
+  std::vector<int64_t> seg;
+};
+
+static fks_status dedup_inputs(const BuildIn& in, const Alloc& A, cudaStream_t st, DedupOut* out) {
+  const bool str = in.kind == FKS_KEY_BYTES;
+  const uint32_t m = in.m;
+  const uint64_t u = uint64_t(in.seg[m]);
+  const int sms = sm_count();
+  uint64_t ctx_bytes = 0;
+  if (str) {
+    int64_t last = 0;
+    FKS_CUDA(cudaMemcpyAsync(&last, in.offs + u, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    FKS_CUDA(cudaStreamSynchronize(st));
+    if (last < 0 || last >= (int64_t(1) << 40)) return fail(FKS_ERR_INVALID_ARG, "offsets out of range");
+    ctx_bytes = uint64_t(last);
+  }
+  const size_t tw = dedup_table_words(u);
+  Carve c;
+  const size_t o_tab = c.take<uint64_t>(tw);
+  const size_t o_pos = c.take<uint32_t>(u + 1);
+  const size_t o_sum = c.take<uint64_t>(scan_sum_words(u + 1));
+  const size_t o_flag = c.take<uint32_t>(4);
+  const size_t o_seg = c.take<int64_t>(m > 1 ? m + 1 : 0);
+  const size_t o_oseg = c.take<int64_t>(m + 1);
+  const size_t o_keys = c.take<uint64_t>(str ? 0 : u);
+  const size_t o_vals = c.take<int64_t>(u);
+  const size_t o_offs = c.take<int64_t>(str ? u + 1 : 0);
+  const size_t o_lens = c.take<uint64_t>(str ? u + 1 : 0);
+  const size_t o_ctx = c.take<uint8_t>(str ? ctx_bytes + 16 : 0);
+  uint8_t* b = static_cast<uint8_t*>(A.get(c.off, st));
+  if (!b) return fail(FKS_ERR_OUT_OF_MEMORY, "allocation of the deduplication buffers failed");
+  out->block = b;
+  out->bytes = c.off;
+  uint32_t* pos = reinterpret_cast<uint32_t*>(b + o_pos);
+  uint32_t* flags = reinterpret_cast<uint32_t*>(b + o_flag);
+  int64_t* d_seg = m > 1 ? reinterpret_cast<int64_t*>(b + o_seg) : nullptr;
+  int64_t* oseg = reinterpret_cast<int64_t*>(b + o_oseg);
+  if (d_seg) FKS_CUDA(cudaMemcpyAsync(d_seg, in.seg, sizeof(int64_t) * (m + 1), cudaMemcpyHostToDevice, st));
+  FKS_CUDA(launch_dedup_mark(str ? nullptr : in.keys, in.ctx, in.offs, d_seg, m, u,
+                             reinterpret_cast<uint64_t*>(b + o_tab), tw, pos, flags, sms, st));
+  FKS_CUDA(scan_exclusive<uint32_t>(pos, u + 1, reinterpret_cast<uint32_t*>(b + o_sum), st));
+  uint32_t h[3] = {0, 0, 0};
+  FKS_CUDA(cudaMemcpyAsync(h, flags, sizeof(uint32_t) * 2, cudaMemcpyDeviceToHost, st));
+  FKS_CUDA(cudaMemcpyAsync(h + 2, pos + u, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+  FKS_CUDA(cudaStreamSynchronize(st));
+  if (h[0]) return fail(FKS_ERR_INVALID_ARG, "bad string offsets");
+  if (h[1]) return fail(FKS_ERR_CUDA, "deduplication table probe limit reached");
+  const int i64 = in.vt == FKS_VAL_I64;
+  void* ovals = b + o_vals;
+  BuildIn r = in;
+  r.vals = ovals;
+  if (!str) {
+    uint64_t* okeys = reinterpret_cast<uint64_t*>(b + o_keys);
+    FKS_CUDA(launch_dedup_pack_u64(in.keys, in.vals, i64, u, pos, okeys, ovals, sms, st));
+    r.keys = okeys;
+  } else {
+    uint64_t* lens = reinterpret_cast<uint64_t*>(b + o_lens);
+    int64_t* ooffs = reinterpret_cast<int64_t*>(b + o_offs);
+    uint8_t* octx = b + o_ctx;
+    FKS_CUDA(launch_dedup_lengths(in.offs, u, pos, lens, sms, st));
+    FKS_CUDA(scan_exclusive<uint64_t>(lens, u + 1, reinterpret_cast<uint64_t*>(b + o_sum), st));
+    FKS_CUDA(launch_dedup_pack_bytes(in.ctx, in.offs, in.vals, i64, u, pos, lens, octx, ooffs, ovals, sms, st));
+    r.ctx = octx;
+    r.offs = ooffs;
+  }
+  out->seg.assign(m + 1, 0);
+  if (m > 1) {
+    FKS_CUDA(launch_dedup_segs(pos, d_seg, m, oseg, st));
+    FKS_CUDA(cudaMemcpyAsync(out->seg.data(), oseg, sizeof(int64_t) * (m + 1), cudaMemcpyDeviceToHost, st));
+    FKS_CUDA(cudaStreamSynchronize(st));
+  } else {
+    out->seg[1] = int64_t(h[2]);
+  }
+  r.seg = out->seg.data();
+  out->in = r;
+  return FKS_OK;
+}
+
 static fks_status build_single(const BuildIn& in, const fks_build_opts* opts,
                                const fks_allocator* alloc, cudaStream_t st, fks_map_t* out) {
   Opts o;
@@ -635,7 +725,16 @@ static fks_status build_single(const BuildIn& in, const fks_build_opts* opts,
   std::vector<fks_map> maps;
   std::vector<fks_status> per;
   sm_count();
-  fks_status s = build_impl(in, o, A, st, &block, &bb, &mem, &maps, &per);
+  DedupOut dd;
+  if (o.dedup) {
+    const fks_status ds = dedup_inputs(in, A, st, &dd);
+    if (ds != FKS_OK) {
+      if (dd.block) A.put(dd.block, dd.bytes, st);
+      return ds;
+    }
+  }
+  fks_status s = build_impl(o.dedup ? dd.in : in, o, A, st, &block, &bb, &mem, &maps, &per);
+  if (dd.block) A.put(dd.block, dd.bytes, st);
   if (s != FKS_OK) return s;
   if (per[0] != FKS_OK) {
     A.put(block, bb, st);
@@ -748,7 +847,16 @@ fks_status fks_build_batched(fks_key_kind kind, const uint64_t* keys, const uint
   std::vector<fks_map> maps;
   std::vector<fks_status> per;
   sm_count();
-  fks_status s = build_impl(in, o, A, st, &block, &bb, &mem, &maps, &per);
+  DedupOut dd;
+  if (o.dedup) {
+    const fks_status ds = dedup_inputs(in, A, st, &dd);
+    if (ds != FKS_OK) {
+      if (dd.block) A.put(dd.block, dd.bytes, st);
+      return ds;
+    }
+  }
+  fks_status s = build_impl(o.dedup ? dd.in : in, o, A, st, &block, &bb, &mem, &maps, &per);
+  if (dd.block) A.put(dd.block, dd.bytes, st);
   if (s != FKS_OK) return s;
   fks_status worst = FKS_OK;
   for (uint32_t j = 0; j < m; ++j) {

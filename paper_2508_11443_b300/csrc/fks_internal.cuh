@@ -145,6 +145,30 @@ size_t split_hist_words(const SplitShape& sh);
 size_t split_sum_words(const SplitShape& sh);
 cudaError_t launch_split(const PassDev& p, const SplitDev& s, bool strings, cudaStream_t stream);
 
+// Device-wide exclusive scan of n elements in place (fks_split.cu); sums
+// holds scan_sum_words(n) elements of scratch.  T = uint32_t or uint64_t.
+template <class T>
+cudaError_t scan_exclusive(T* data, uint64_t n, T* sums, cudaStream_t st);
+size_t scan_sum_words(uint64_t n);
+
+// from_array pre-pass (fks_dedup.cu).  launch_dedup_mark fills keep[0 .. u]
+// (keep[u] = 0) with the first-occurrence flags; flags[0] = malformed string
+// offsets, flags[1] = a probe sequence ran out (not expected).  After an
+// in-place exclusive scan of keep (= pos), the pack launchers gather the
+// kept elements in input order.
+size_t dedup_table_words(uint64_t u);
+cudaError_t launch_dedup_mark(const uint64_t* keys, const uint8_t* ctx, const int64_t* offs, const int64_t* d_seg,
+                              uint32_t m, uint64_t u, uint64_t* table, size_t table_words, uint32_t* keep,
+                              uint32_t* flags, int sms, cudaStream_t st);
+cudaError_t launch_dedup_pack_u64(const uint64_t* keys, const void* vals, int vals_i64, uint64_t u,
+                                  const uint32_t* pos, uint64_t* okeys, void* ovals, int sms, cudaStream_t st);
+cudaError_t launch_dedup_lengths(const int64_t* offs, uint64_t u, const uint32_t* pos, uint64_t* lens, int sms,
+                                 cudaStream_t st);
+cudaError_t launch_dedup_pack_bytes(const uint8_t* ctx, const int64_t* offs, const void* vals, int vals_i64,
+                                    uint64_t u, const uint32_t* pos, const uint64_t* noff, uint8_t* octx,
+                                    int64_t* ooffs, void* ovals, int sms, cudaStream_t st);
+cudaError_t launch_dedup_segs(const uint32_t* pos, const int64_t* d_seg, uint32_t m, int64_t* oseg, cudaStream_t st);
+
 // Launchers (fks_build.cu).
 cudaError_t launch_fingerprints(const uint8_t* ctx, const int64_t* offs, uint64_t n,
                                 const MapDev* maps, const uint64_t* pass_seg, uint32_t m,

@@ -14,6 +14,7 @@
 #include <stdint.h>
 
 #include "fks_internal.cuh"
+#include "fks_strings.cuh"
 
 namespace fks {
 namespace {
@@ -43,21 +44,6 @@ __device__ __forceinline__ ulonglong2 ld_na_u128(const uint64_t* p, uint64_t pol
                : "=l"(v.x), "=l"(v.y)
                : "l"(p), "l"(pol));
   return v;
-}
-
-// t-th little-endian 32-bit word of s[0 .. len), zero padded; reads only
-// aligned words holding at least one byte of the string.
-__device__ __forceinline__ uint32_t str_word(const uint8_t* s, uint32_t len, uint32_t t) {
-  const uintptr_t a = reinterpret_cast<uintptr_t>(s) + 4u * t;
-  const uint32_t r = len - 4u * t;
-  const uint32_t take = r < 4u ? r : 4u;
-  const uint32_t sh = uint32_t(a & 3u);
-  const uint32_t* A = reinterpret_cast<const uint32_t*>(a & ~uintptr_t(3));
-  const uint32_t lo = __ldg(A);
-  const uint32_t hi = (sh + take > 4u) ? __ldg(A + 1) : 0u;
-  uint32_t w = __funnelshift_r(lo, hi, sh * 8u);
-  if (take < 4u) w &= (1u << (8u * take)) - 1u;
-  return w;
 }
 
 template <int kQ, bool kI64>
@@ -147,9 +133,7 @@ __global__ void __launch_bounds__(kLookupThreads) k_lookup_u64(LookupMap M,
 __device__ __forceinline__ bool lookup_one_bytes(const LookupMap& M, const uint8_t* s,
                                                  uint32_t len, int64_t* val) {
   const uint64_t keep = policy_keep(), strm = policy_stream();
-  uint64_t h = len;
-  const uint32_t words = (len + 3u) >> 2;
-  for (uint32_t t = 0; t < words; ++t) h = addmod61(mulmod61(h, M.fpb), str_word(s, len, t));
+  const uint64_t h = fingerprint(s, len, M.fpb);
   const uint32_t b = reduce32(hash32(M.c1, h), M.nb);
   const uint64_t d = ld_na_u64(M.desc + b, keep);
   const uint32_t sz = desc_s(d);
@@ -158,9 +142,7 @@ __device__ __forceinline__ bool lookup_one_bytes(const LookupMap& M, const uint8
   const uint32_t jj = desc_off(d) + reduce32(hash32(c, h), sz * sz);
   const ulonglong2 w0 = ld_na_u128(M.slots + 4ull * jj, strm);
   if (w0.x != h || offlen_len(w0.y) != len) return false;
-  const uint8_t* ms = M.ctx + offlen_off(w0.y);
-  for (uint32_t t = 0; t < words; ++t)
-    if (str_word(ms, len, t) != str_word(s, len, t)) return false;
+  if (!bytes_equal(M.ctx + offlen_off(w0.y), s, len)) return false;
   *val = int64_t(ld_na_u64(M.slots + 4ull * jj + 2, strm));
   return true;
 }

@@ -348,38 +348,41 @@ __global__ void __launch_bounds__(256) k_part_starts(PassDev p, SplitDev s) {
   }
 }
 
-// ------------------------------------------------------------ device-wide exclusive scan (u32)
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* in, uint64_t n, uint32_t* sums) {
-  __shared__ uint32_t ws[kScanThreads / 32];
+// ------------------------------------------------------------ device-wide exclusive scan
+template <class T>
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const T* in, uint64_t n, T* sums) {
+  __shared__ T ws[kScanThreads / 32];
   const uint64_t b0 = uint64_t(blockIdx.x) * kScanItems;
-  uint32_t v = 0;
+  T v = 0;
   for (uint64_t i = b0 + threadIdx.x; i < min(n, b0 + kScanItems); i += kScanThreads) v += in[i];
-  v = __reduce_add_sync(0xFFFFFFFFu, v);
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, d);
   if (lane() == 0) ws[threadIdx.x >> 5] = v;
   __syncthreads();
   if (threadIdx.x == 0) {
-    uint32_t tot = 0;
+    T tot = 0;
     for (int w = 0; w < kScanThreads / 32; ++w) tot += ws[w];
     sums[blockIdx.x] = tot;
   }
 }
 
-__global__ void __launch_bounds__(1024) k_scan_sums(uint32_t* sums, uint32_t nb) {
-  __shared__ uint32_t ws[32];
-  __shared__ uint32_t carry;
+template <class T>
+__global__ void __launch_bounds__(1024) k_scan_sums(T* sums, uint32_t nb) {
+  __shared__ T ws[32];
+  __shared__ T carry;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
   for (uint32_t c0 = 0; c0 < nb; c0 += 1024) {
     const uint32_t i = c0 + threadIdx.x;
-    const uint32_t v = i < nb ? sums[i] : 0u;
-    uint32_t inc = v;
+    const T v = i < nb ? sums[i] : T(0);
+    T inc = v;
     for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, d);
+      const T y = __shfl_up_sync(0xFFFFFFFFu, inc, d);
       if (lane() >= uint32_t(d)) inc += y;
     }
     if (lane() == 31) ws[threadIdx.x >> 5] = inc;
     __syncthreads();
-    uint32_t base = carry;
+    T base = carry;
     for (uint32_t w = 0; w < (threadIdx.x >> 5); ++w) base += ws[w];
     if (i < nb) sums[i] = base + inc - v;
     __syncthreads();
@@ -388,24 +391,25 @@ __global__ void __launch_bounds__(1024) k_scan_sums(uint32_t* sums, uint32_t nb)
   }
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_down(uint32_t* data, uint64_t n, const uint32_t* sums) {
-  __shared__ uint32_t ws[kScanThreads / 32];
+template <class T>
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(T* data, uint64_t n, const T* sums) {
+  __shared__ T ws[kScanThreads / 32];
   constexpr uint32_t kPer = kScanItems / kScanThreads;  // 16 consecutive per thread
   const uint64_t b0 = uint64_t(blockIdx.x) * kScanItems + uint64_t(threadIdx.x) * kPer;
-  uint32_t v[kPer], sum = 0;
+  T v[kPer], sum = 0;
 #pragma unroll
   for (uint32_t q = 0; q < kPer; ++q) {
-    v[q] = b0 + q < n ? data[b0 + q] : 0u;
+    v[q] = b0 + q < n ? data[b0 + q] : T(0);
     sum += v[q];
   }
-  uint32_t inc = sum;
+  T inc = sum;
   for (int d = 1; d < 32; d <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, d);
+    const T y = __shfl_up_sync(0xFFFFFFFFu, inc, d);
     if (lane() >= uint32_t(d)) inc += y;
   }
   if (lane() == 31) ws[threadIdx.x >> 5] = inc;
   __syncthreads();
-  uint32_t run = sums[blockIdx.x];
+  T run = sums[blockIdx.x];
   for (uint32_t w = 0; w < (threadIdx.x >> 5); ++w) run += ws[w];
   run += inc - sum;
 #pragma unroll
@@ -415,16 +419,22 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(uint32_t* data, uint
   }
 }
 
-cudaError_t scan_u32(uint32_t* data, uint64_t n, uint32_t* sums, cudaStream_t st) {
+}  // namespace
+
+template <class T>
+cudaError_t scan_exclusive(T* data, uint64_t n, T* sums, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   const uint32_t nb = uint32_t((n + kScanItems - 1) / kScanItems);
-  k_scan_reduce<<<nb, kScanThreads, 0, st>>>(data, n, sums);
-  k_scan_sums<<<1, 1024, 0, st>>>(sums, nb);
-  k_scan_down<<<nb, kScanThreads, 0, st>>>(data, n, sums);
+  k_scan_reduce<T><<<nb, kScanThreads, 0, st>>>(data, n, sums);
+  k_scan_sums<T><<<1, 1024, 0, st>>>(sums, nb);
+  k_scan_down<T><<<nb, kScanThreads, 0, st>>>(data, n, sums);
+  note_launches(3);
   return cudaGetLastError();
 }
+template cudaError_t scan_exclusive<uint32_t>(uint32_t*, uint64_t, uint32_t*, cudaStream_t);
+template cudaError_t scan_exclusive<uint64_t>(uint64_t*, uint64_t, uint64_t*, cudaStream_t);
 
-}  // namespace
+size_t scan_sum_words(uint64_t n) { return size_t((n + kScanItems - 1) / kScanItems) + 2; }
 
 SplitShape split_shape(uint32_t P, uint64_t total) {
   SplitShape sh{};
@@ -464,7 +474,7 @@ cudaError_t launch_split(const PassDev& p, const SplitDev& s, bool strings, cuda
   }
   k_countA<<<s.tilesA, kSplitThreads, 0, st>>>(p, s);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = scan_u32(s.histA, uint64_t(s.binsA) * s.tilesA, s.sums, st)) != cudaSuccess) return e;
+  if ((e = scan_exclusive<uint32_t>(s.histA, uint64_t(s.binsA) * s.tilesA, s.sums, st)) != cudaSuccess) return e;
   if (strings) k_scatterA<true><<<s.tilesA, kSplitThreads, smemA, st>>>(p, s);
   else k_scatterA<false><<<s.tilesA, kSplitThreads, smemA, st>>>(p, s);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -473,14 +483,14 @@ cudaError_t launch_split(const PassDev& p, const SplitDev& s, bool strings, cuda
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   // entries past the last real level-B tile are never written or read; they
   // only trail the real ones in the scan
-  if ((e = scan_u32(s.histB, uint64_t(s.binsB) * s.tilesB_max, s.sums, st)) != cudaSuccess) return e;
+  if ((e = scan_exclusive<uint32_t>(s.histB, uint64_t(s.binsB) * s.tilesB_max, s.sums, st)) != cudaSuccess) return e;
   if (strings) k_scatterB<true><<<s.tilesB_max, kSplitThreads, smemB, st>>>(p, s);
   else k_scatterB<false><<<s.tilesB_max, kSplitThreads, smemB, st>>>(p, s);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   uint32_t blocks = (p.P + 255) / 256;
   if (blocks > 2048) blocks = 2048;
   k_part_starts<<<blocks, 256, 0, st>>>(p, s);
-  note_launches(12);
+  note_launches(6);  // the two scans count their own three
   return cudaGetLastError();
 }
 

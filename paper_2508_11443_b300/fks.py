@@ -39,7 +39,7 @@ class fks_build_opts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_size_t), ("bound_factor", ctypes.c_uint32),
                 ("attempt_cap", ctypes.c_uint32), ("round_cap", ctypes.c_uint32),
                 ("reject_attempts", ctypes.c_uint32), ("spin_limit", ctypes.c_uint32),
-                ("keys_per_bucket", ctypes.c_uint32)]
+                ("keys_per_bucket", ctypes.c_uint32), ("dedup", ctypes.c_uint32)]
 
 
 class fks_map_info_t(ctypes.Structure):
