@@ -83,6 +83,10 @@ def lib():
         L.or_fingerprints.argtypes = [vp, vp, u64, u64, u32, vp]
         L.or_dedup.restype = u64
         L.or_dedup.argtypes = [vp, vp, vp, u64, vp, u32, vp]
+        L.or_eytzinger_layout.restype = None
+        L.or_eytzinger_layout.argtypes = [vp, vp, u64, vp, vp]
+        L.or_eytzinger_search.restype = u64
+        L.or_eytzinger_search.argtypes = [vp, u64, u64]
         L.or_binary_search.restype = ctypes.c_int64
         L.or_binary_search.argtypes = [vp, u64, u64]
         _lib = L
@@ -289,6 +293,23 @@ def from_array_u64(keys, vals, seed: int, **opts) -> Map:
     """from_array over uint64 keys: duplicates allowed, first occurrence wins."""
     keep = dedup_keep(keys=keys).astype(bool)
     return build_u64(np.asarray(keys, np.uint64)[keep], np.asarray(vals, np.int64)[keep], seed, **opts)
+
+
+def eytzinger_layout(sorted_keys, sorted_vals):
+    """(keys, values) in Eytzinger order, 1-based: index 0 is unused (0)."""
+    sk = _c(sorted_keys, np.uint64)
+    sv = _c(sorted_vals, np.int64)
+    n = sk.size
+    ek = np.zeros(n + 1, np.uint64)
+    ev = np.zeros(n + 1, np.int64)
+    lib().or_eytzinger_layout(_p(sk), _p(sv), n, _p(ek), _p(ev))
+    return ek, ev
+
+
+def eytzinger_search(ek, q: int) -> int:
+    """Node of q in an Eytzinger array (1-based), or 0 when absent."""
+    e = _c(ek, np.uint64)
+    return int(lib().or_eytzinger_search(_p(e), e.size - 1, q & (2**64 - 1)))
 
 
 def binary_search(sorted_keys, q: int) -> int:

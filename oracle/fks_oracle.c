@@ -582,6 +582,46 @@ void or_fingerprints(const uint8_t* ctx, const int64_t* offs, uint64_t n, uint64
     out[i] = or_fingerprint(ctx + offs[i], (uint64_t)(offs[i + 1] - offs[i]), base);
 }
 
+/* Eytzinger layout (Sec. 3.4, the locality variant of the sorted-array map):
+ * the implicit binary search tree of the sorted keys stored level by level.
+ * e[1..n] (1-based; e[0] unused): node k has children 2k and 2k+1, and an
+ * in-order walk of the tree visits the keys in sorted order.  Filled here
+ * by that definition: an in-order traversal that assigns sorted[0], [1], ...
+ * to the nodes it visits. */
+static void or_eyt_fill(const uint64_t* sk, const int64_t* sv, uint64_t n, uint64_t k, uint64_t* next,
+                        uint64_t* ek, int64_t* ev) {
+  if (k > n) return;
+  or_eyt_fill(sk, sv, n, 2 * k, next, ek, ev);
+  ek[k] = sk[*next];
+  ev[k] = sv[*next];
+  *next += 1;
+  or_eyt_fill(sk, sv, n, 2 * k + 1, next, ek, ev);
+}
+
+void or_eytzinger_layout(const uint64_t* sorted_keys, const int64_t* sorted_vals, uint64_t n, uint64_t* ek,
+                         int64_t* ev) {
+  uint64_t next = 0;
+  ek[0] = 0;
+  ev[0] = 0;
+  or_eyt_fill(sorted_keys, sorted_vals, n, 1, &next, ek, ev);
+}
+
+/* Search of the Eytzinger array: descend k -> 2k + (e[k] < q) until k > n;
+ * the last node where the walk went left holds the smallest key >= q.
+ * Returns that node if its key equals q, else 0. */
+uint64_t or_eytzinger_search(const uint64_t* ek, uint64_t n, uint64_t q) {
+  uint64_t k = 1, cand = 0;
+  while (k <= n) {
+    if (ek[k] < q) {
+      k = 2 * k + 1;
+    } else {
+      cand = k;
+      k = 2 * k;
+    }
+  }
+  return (cand && ek[cand] == q) ? cand : 0;
+}
+
 /* Sorted-array map (Sec. 3.4, mk_arraymap): binary search returning the
  * index or -1; used as the search-based comparison point. */
 int64_t or_binary_search(const uint64_t* sorted, uint64_t n, uint64_t q) {

@@ -538,3 +538,54 @@ def test_from_array_lookups_follow_first_occurrence():
     out, found = O.lookup_u64(m, q)
     for k, v, f in zip(q.tolist(), out.tolist(), found.tolist()):
         assert f == (k in first) and v == first.get(k, -1)
+
+
+# ------------------------------------------------------------------ Eytzinger layout
+def _inorder(ek, n, k=1, out=None):
+    out = [] if out is None else out
+    if k <= n:
+        _inorder(ek, n, 2 * k, out)
+        out.append(int(ek[k]))
+        _inorder(ek, n, 2 * k + 1, out)
+    return out
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 7, 8, 15, 100, 1023, 1024, 5000])
+def test_eytzinger_layout_is_the_level_order_tree(n):
+    rng = np.random.default_rng(n)
+    sk = np.sort(np.unique(rng.integers(0, 2**64, n + 50, dtype=np.uint64, endpoint=False)))[:n]
+    sv = rng.integers(-2**40, 2**40, n)
+    ek, ev = O.eytzinger_layout(sk, sv)
+    # a permutation whose in-order walk is the sorted order, values travel with keys
+    assert _inorder(ek, n) == sk.tolist()
+    pos = {int(k): i for i, k in enumerate(sk.tolist())}
+    assert all(ev[k] == sv[pos[int(ek[k])]] for k in range(1, n + 1))
+    # heap order: a node is greater than its left child and smaller than its right child
+    for k in range(1, n + 1):
+        if 2 * k <= n:
+            assert ek[2 * k] < ek[k]
+        if 2 * k + 1 <= n:
+            assert ek[2 * k + 1] > ek[k]
+
+
+def test_eytzinger_perfect_tree_root_is_the_median():
+    for h in range(1, 12):
+        n = (1 << h) - 1
+        sk = np.arange(n, dtype=np.uint64) * np.uint64(3) + np.uint64(1)
+        ek, _ = O.eytzinger_layout(sk, np.arange(n))
+        assert ek[1] == sk[n // 2]
+        # the last level holds every other key, in order
+        assert ek[(n + 1) // 2: n + 1].tolist() == sk[0::2].tolist()
+
+
+def test_eytzinger_search_matches_binary_search():
+    rng = np.random.default_rng(9)
+    for n in (1, 2, 3, 10, 777, 4096):
+        sk = np.sort(np.unique(rng.integers(0, 1 << 20, n * 2, dtype=np.uint64)))[:n]
+        ek, ev = O.eytzinger_layout(sk, np.arange(sk.size))
+        for q in rng.integers(0, (1 << 20) + 5, 300, dtype=np.uint64).tolist() + [0, 2**64 - 1] + sk[:5].tolist():
+            k = O.eytzinger_search(ek, q)
+            i = O.binary_search(sk, q)
+            assert (k != 0) == (i >= 0)
+            if k:
+                assert ek[k] == q and ev[k] == i
