@@ -648,11 +648,30 @@ def main():
                 sl.append(a1.elapsed_time(a2))
             del sm
         assert np.array_equal(found.cpu().numpy(), w.expect_found)
+        eb, el = [], []
+        for i in range(4):
+            a0, a1, a2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            a0.record(stream)
+            em = F.fks_eytzmap_build(keys, vals)
+            a1.record(stream)
+            F.fks_sortmap_lookup(em, queries, out, found, -1)
+            a2.record(stream)
+            torch.cuda.synchronize()
+            if i >= 1:
+                eb.append(a0.elapsed_time(a1))
+                el.append(a1.elapsed_time(a2))
+            del em
+        assert np.array_equal(found.cpu().numpy(), w.expect_found)
+        assert np.array_equal(out.cpu().numpy(), np.where(w.expect_found == 1, w.expect_vals, -1))
         line["search_baseline"] = {
             "what": "GPU LSD radix sort of (key, value) + binary-search lookup, same data",
             "build_ms": med(sb), "lookup_ms": med(sl),
             "build_keys_per_s": n / (med(sb) / 1e3), "lookups_per_s": nq / (med(sl) / 1e3),
-            "fks_speedup_build": med(sb) / med(build_ms), "fks_speedup_lookup": med(sl) / lk}
+            "fks_speedup_build": med(sb) / med(build_ms), "fks_speedup_lookup": med(sl) / lk,
+            "eytzinger": {"what": "the same sort, gathered into Eytzinger order; lookups descend the tree",
+                          "build_ms": med(eb), "lookup_ms": med(el),
+                          "lookups_per_s": nq / (med(el) / 1e3),
+                          "fks_speedup_build": med(eb) / med(build_ms), "fks_speedup_lookup": med(el) / lk}}
     # ---- the other rows of the path: string keys (config 3), batched maps (config 4)
     if not args.no_extras:
         line["bucket_variants"] = run_bucket_variants(F, torch, hbm, keys, vals, queries, out, found, w, n, nq)

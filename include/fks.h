@@ -258,7 +258,16 @@ fks_status fks_sortmap_build(const uint64_t* keys, const void* vals, fks_val_typ
                              const fks_allocator* alloc, fks_stream_t stream, fks_sortmap_t* out);
 fks_status fks_sortmap_lookup(fks_sortmap_t map, const uint64_t* q, uint64_t nq, void* out_vals,
                               uint8_t* out_found, int64_t absent, fks_stream_t stream);
-/* sorted keys and their values (int64) to host memory; synchronises */
+/* fks_eytzmap_build -- the paper's locality variant of the same map (Sec. 3.4;
+ * the third row of its Table 1): the sorted pairs stored in Eytzinger order,
+ * the implicit binary search tree level by level (node k, 1-based, has
+ * children 2k and 2k + 1), so the top levels a search visits first are
+ * contiguous and stay cached.  The result is an fks_sortmap_t: lookups go
+ * through fks_sortmap_lookup, which descends the tree. */
+fks_status fks_eytzmap_build(const uint64_t* keys, const void* vals, fks_val_type val_type, uint64_t n,
+                             const fks_allocator* alloc, fks_stream_t stream, fks_sortmap_t* out);
+/* keys and their values (int64) to host memory in storage order: sorted, or
+ * Eytzinger order (nodes 1..n) for maps from fks_eytzmap_build; synchronises */
 fks_status fks_sortmap_export(fks_sortmap_t map, uint64_t* h_keys, int64_t* h_vals, fks_stream_t stream);
 void fks_sortmap_destroy(fks_sortmap_t map);
 

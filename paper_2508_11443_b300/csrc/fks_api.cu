@@ -201,7 +201,8 @@ struct fks_mapset {
 struct fks_sortmap {
   fks_val_type vt = FKS_VAL_I64;
   uint64_t n = 0;
-  uint64_t* keys = nullptr;  // sorted
+  int eytzinger = 0;         // 0: sorted order; 1: Eytzinger order, 1-based (n + 1 words)
+  uint64_t* keys = nullptr;
   uint64_t* vals = nullptr;  // int64 words
   void* block = nullptr;
   size_t block_bytes = 0;
@@ -973,23 +974,28 @@ void fks_mapset_destroy(fks_mapset_t set) {
   delete set;
 }
 
-fks_status fks_sortmap_build(const uint64_t* keys, const void* vals, fks_val_type val_type, uint64_t n,
-                             const fks_allocator* alloc, fks_stream_t stream, fks_sortmap_t* out) {
+// Sorted (keys, values) of n pairs into a new map: layout 0 keeps the sorted
+// order, layout 1 gathers it into Eytzinger order.
+static fks_status sortmap_build(const uint64_t* keys, const void* vals, fks_val_type val_type, uint64_t n,
+                                int eytzinger, const fks_allocator* alloc, fks_stream_t stream, fks_sortmap_t* out,
+                                const char* who) {
   if (!out) return fail(FKS_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (!keys || !vals || n == 0 || n >= (1ull << 32) || (val_type != FKS_VAL_I32 && val_type != FKS_VAL_I64))
-    return fail(FKS_ERR_INVALID_ARG, "fks_sortmap_build: bad arguments");
+    return fail(FKS_ERR_INVALID_ARG, std::string(who) + ": bad arguments");
   sm_count();
   Alloc A(alloc);
   const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const size_t bytes = 16 * n;
+  const uint64_t words = eytzinger ? n + 1 : n;
+  const size_t bytes = 16 * words;
   uint8_t* block = static_cast<uint8_t*>(A.get(bytes, st));
-  if (!block) return fail(FKS_ERR_OUT_OF_MEMORY, "fks_sortmap_build: tables");
-  const size_t sbytes = sort_scratch_bytes(n) + (val_type == FKS_VAL_I32 ? 8 * n : 0);
+  if (!block) return fail(FKS_ERR_OUT_OF_MEMORY, std::string(who) + ": tables");
+  const size_t sorted_bytes = eytzinger ? 16 * n : 0;  // sorted pairs before the gather
+  const size_t sbytes = sort_scratch_bytes(n) + (val_type == FKS_VAL_I32 ? 8 * n : 0) + sorted_bytes;
   uint8_t* scr = static_cast<uint8_t*>(A.get(sbytes, st));
   if (!scr) {
     A.put(block, bytes, st);
-    return fail(FKS_ERR_OUT_OF_MEMORY, "fks_sortmap_build: scratch");
+    return fail(FKS_ERR_OUT_OF_MEMORY, std::string(who) + ": scratch");
   }
   const uint64_t* v64 = static_cast<const uint64_t*>(vals);
   cudaError_t e = cudaSuccess;
@@ -1001,19 +1007,37 @@ fks_status fks_sortmap_build(const uint64_t* keys, const void* vals, fks_val_typ
   fks_sortmap* m = new fks_sortmap();
   m->vt = val_type;
   m->n = n;
+  m->eytzinger = eytzinger;
   m->keys = reinterpret_cast<uint64_t*>(block);
-  m->vals = m->keys + n;
+  m->vals = m->keys + words;
   m->block = block;
   m->block_bytes = bytes;
   m->alloc = A;
-  if (e == cudaSuccess) e = launch_sort_pairs(keys, v64, n, m->keys, m->vals, scr, st);
+  if (!eytzinger) {
+    if (e == cudaSuccess) e = launch_sort_pairs(keys, v64, n, m->keys, m->vals, scr, st);
+  } else {
+    uint64_t* sk = reinterpret_cast<uint64_t*>(scr + sbytes - sorted_bytes);
+    uint64_t* sv = sk + n;
+    if (e == cudaSuccess) e = launch_sort_pairs(keys, v64, n, sk, sv, scr, st);
+    if (e == cudaSuccess) e = launch_eytzinger_layout(sk, sv, n, m->keys, m->vals, sm_count(), st);
+  }
   A.put(scr, sbytes, st);
   if (e != cudaSuccess) {
     fks_sortmap_destroy(m);
-    return cuda_fail(e, "fks_sortmap_build");
+    return cuda_fail(e, who);
   }
   *out = m;
   return FKS_OK;
+}
+
+fks_status fks_sortmap_build(const uint64_t* keys, const void* vals, fks_val_type val_type, uint64_t n,
+                             const fks_allocator* alloc, fks_stream_t stream, fks_sortmap_t* out) {
+  return sortmap_build(keys, vals, val_type, n, 0, alloc, stream, out, "fks_sortmap_build");
+}
+
+fks_status fks_eytzmap_build(const uint64_t* keys, const void* vals, fks_val_type val_type, uint64_t n,
+                             const fks_allocator* alloc, fks_stream_t stream, fks_sortmap_t* out) {
+  return sortmap_build(keys, vals, val_type, n, 1, alloc, stream, out, "fks_eytzmap_build");
 }
 
 fks_status fks_sortmap_lookup(fks_sortmap_t map, const uint64_t* q, uint64_t nq, void* out_vals,
@@ -1022,16 +1046,21 @@ fks_status fks_sortmap_lookup(fks_sortmap_t map, const uint64_t* q, uint64_t nq,
   if (nq == 0) return FKS_OK;
   if (!q || (map->vt == FKS_VAL_I32 && (absent < INT32_MIN || absent > INT32_MAX)))
     return fail(FKS_ERR_INVALID_ARG, "fks_sortmap_lookup: bad arguments");
-  FKS_CUDA(launch_sorted_search(map->keys, map->vals, map->n, q, nq, out_vals, map->vt == FKS_VAL_I64, out_found,
-                                absent, sm_count(), reinterpret_cast<cudaStream_t>(stream)));
+  if (map->eytzinger)
+    FKS_CUDA(launch_eytzinger_search(map->keys, map->vals, map->n, q, nq, out_vals, map->vt == FKS_VAL_I64,
+                                     out_found, absent, sm_count(), reinterpret_cast<cudaStream_t>(stream)));
+  else
+    FKS_CUDA(launch_sorted_search(map->keys, map->vals, map->n, q, nq, out_vals, map->vt == FKS_VAL_I64, out_found,
+                                  absent, sm_count(), reinterpret_cast<cudaStream_t>(stream)));
   return FKS_OK;
 }
 
 fks_status fks_sortmap_export(fks_sortmap_t map, uint64_t* h_keys, int64_t* h_vals, fks_stream_t stream) {
   if (!map) return fail(FKS_ERR_INVALID_ARG, "fks_sortmap_export: NULL map");
   const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (h_keys) FKS_CUDA(cudaMemcpyAsync(h_keys, map->keys, 8 * map->n, cudaMemcpyDeviceToHost, st));
-  if (h_vals) FKS_CUDA(cudaMemcpyAsync(h_vals, map->vals, 8 * map->n, cudaMemcpyDeviceToHost, st));
+  const uint64_t first = map->eytzinger ? 1 : 0;  // Eytzinger slot 0 is unused
+  if (h_keys) FKS_CUDA(cudaMemcpyAsync(h_keys, map->keys + first, 8 * map->n, cudaMemcpyDeviceToHost, st));
+  if (h_vals) FKS_CUDA(cudaMemcpyAsync(h_vals, map->vals + first, 8 * map->n, cudaMemcpyDeviceToHost, st));
   FKS_CUDA(cudaStreamSynchronize(st));
   return FKS_OK;
 }

@@ -235,5 +235,10 @@ cudaError_t launch_widen_i32(const int32_t* in, uint64_t n, uint64_t* out, cudaS
 cudaError_t launch_sorted_search(const uint64_t* keys, const uint64_t* vals, uint64_t n, const uint64_t* q,
                                  uint64_t nq, void* out, int out_i64, uint8_t* found, int64_t absent, int sms,
                                  cudaStream_t st);
+// Eytzinger layout of sorted (keys, values): ek, ev hold n + 1 words (slot 0 unused).
+cudaError_t launch_eytzinger_layout(const uint64_t* sk, const uint64_t* sv, uint64_t n, uint64_t* ek, uint64_t* ev,
+                                    int sms, cudaStream_t st);
+cudaError_t launch_eytzinger_search(const uint64_t* ek, const uint64_t* ev, uint64_t n, const uint64_t* q, uint64_t nq,
+                                    void* out, int out_i64, uint8_t* found, int64_t absent, int sms, cudaStream_t st);
 
 }  // namespace fks

@@ -21,8 +21,6 @@ constexpr int kSortThreads = 256;  // 8 warps x 256 keys each, 32 per round
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr uint32_t kPerWarp = kSortTile / kSortWarps;
 constexpr uint32_t kRounds = kPerWarp / 32;
-constexpr uint32_t kScanItems = 8192;
-constexpr int kScanThreads = 512;
 
 __device__ __forceinline__ uint32_t lane() { return threadIdx.x & 31u; }
 __device__ __forceinline__ uint32_t lanemask_lt() {
@@ -97,72 +95,6 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const uint64_t* _
   }
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_sum_blocks(const uint32_t* in, uint64_t n, uint32_t* sums) {
-  __shared__ uint32_t ws[kScanThreads / 32];
-  const uint64_t b0 = uint64_t(blockIdx.x) * kScanItems;
-  uint32_t v = 0;
-  for (uint64_t i = b0 + threadIdx.x; i < min(n, b0 + kScanItems); i += kScanThreads) v += in[i];
-  v = __reduce_add_sync(0xFFFFFFFFu, v);
-  if (lane() == 0) ws[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t tot = 0;
-    for (int i = 0; i < kScanThreads / 32; ++i) tot += ws[i];
-    sums[blockIdx.x] = tot;
-  }
-}
-
-__global__ void __launch_bounds__(1024) k_scan_block_sums(uint32_t* sums, uint32_t nb) {
-  __shared__ uint32_t ws[32];
-  __shared__ uint32_t carry;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  for (uint32_t c0 = 0; c0 < nb; c0 += 1024) {
-    const uint32_t i = c0 + threadIdx.x;
-    const uint32_t v = i < nb ? sums[i] : 0u;
-    uint32_t inc = v;
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, d);
-      if (lane() >= uint32_t(d)) inc += y;
-    }
-    if (lane() == 31) ws[threadIdx.x >> 5] = inc;
-    __syncthreads();
-    uint32_t b = carry;
-    for (uint32_t q = 0; q < (threadIdx.x >> 5); ++q) b += ws[q];
-    if (i < nb) sums[i] = b + inc - v;
-    __syncthreads();
-    if (threadIdx.x == 1023) carry = b + inc;
-    __syncthreads();
-  }
-}
-
-__global__ void __launch_bounds__(kScanThreads) k_scan_apply(uint32_t* data, uint64_t n, const uint32_t* sums) {
-  __shared__ uint32_t ws[kScanThreads / 32];
-  constexpr uint32_t kPer = kScanItems / kScanThreads;
-  const uint64_t b0 = uint64_t(blockIdx.x) * kScanItems + uint64_t(threadIdx.x) * kPer;
-  uint32_t v[kPer], sum = 0;
-#pragma unroll
-  for (uint32_t q = 0; q < kPer; ++q) {
-    v[q] = b0 + q < n ? data[b0 + q] : 0u;
-    sum += v[q];
-  }
-  uint32_t inc = sum;
-  for (int d = 1; d < 32; d <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, d);
-    if (lane() >= uint32_t(d)) inc += y;
-  }
-  if (lane() == 31) ws[threadIdx.x >> 5] = inc;
-  __syncthreads();
-  uint32_t run = sums[blockIdx.x];
-  for (uint32_t q = 0; q < (threadIdx.x >> 5); ++q) run += ws[q];
-  run += inc - sum;
-#pragma unroll
-  for (uint32_t q = 0; q < kPer; ++q) {
-    if (b0 + q < n) data[b0 + q] = run;
-    run += v[q];
-  }
-}
-
 // Binary search (lower bound) of each needle; index or absent (Sec. 3.4:
 // binary_search returns -1 for a needle that is not there).
 template <bool kI64>
@@ -193,18 +125,97 @@ __global__ void __launch_bounds__(256) k_search(const uint64_t* __restrict__ key
   }
 }
 
+// ---------------------------------------------------------------- Eytzinger
+// The locality variant of the sorted-array map (Sec. 3.4): the implicit
+// search tree of the sorted keys stored level by level, 1-based (node k has
+// children 2k and 2k + 1; slot 0 unused).  Nodes 1..n form a complete
+// binary tree, so subtree sizes have a closed form and every node finds its
+// in-order rank -- the sorted position of its key -- in O(log n).
+__device__ __forceinline__ uint32_t ilog2(uint64_t v) { return 63u - uint32_t(__clzll(static_cast<long long>(v))); }
+
+// Nodes in the subtree of v (complete tree of n nodes, last level at depth H).
+__device__ __forceinline__ uint64_t subtree_size(uint64_t v, uint64_t n, uint32_t H) {
+  if (v > n) return 0;
+  const uint32_t t = H - ilog2(v);                // levels below v down to the last
+  const uint64_t first = v << t, span = 1ull << t;  // v's nodes on the last level
+  const uint64_t last = first > n ? 0 : (n - first + 1 < span ? n - first + 1 : span);
+  return span - 1 + last;
+}
+
+__device__ __forceinline__ uint64_t inorder_rank(uint64_t k, uint64_t n, uint32_t H) {
+  uint64_t r = subtree_size(2 * k, n, H);
+  for (uint64_t c = k; c > 1; c >>= 1)
+    if (c & 1) r += subtree_size(c - 1, n, H) + 1;  // a right child: the left sibling's subtree and the parent
+  return r;
+}
+
+__global__ void __launch_bounds__(256) k_eytz_gather(const uint64_t* __restrict__ sk, const uint64_t* __restrict__ sv,
+                                                     uint64_t n, uint64_t* __restrict__ ek, uint64_t* __restrict__ ev) {
+  const uint32_t H = ilog2(n);
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t k = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; k <= n; k += stride) {
+    if (k == 0) {
+      ek[0] = 0;
+      ev[0] = 0;
+      continue;
+    }
+    const uint64_t r = inorder_rank(k, n, H);
+    ek[k] = __ldg(sk + r);
+    ev[k] = __ldg(sv + r);
+  }
+}
+
+// Descend k -> 2k + (e[k] < q), kQ needles per thread in step (all their
+// loads of one level in flight together); the answer is the last node where
+// the walk went left, if its key equals the needle.
+template <int kQ, bool kI64>
+__global__ void __launch_bounds__(256) k_eytz_search(const uint64_t* __restrict__ ek, const uint64_t* __restrict__ ev,
+                                                     uint64_t n, const uint64_t* __restrict__ q, uint64_t nq,
+                                                     void* __restrict__ out, uint8_t* __restrict__ found,
+                                                     int64_t absent) {
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x * kQ;
+  for (uint64_t base = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) * kQ; base < nq; base += stride) {
+    uint64_t x[kQ], k[kQ], cand[kQ];
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      x[i] = base + i < nq ? __ldcs(q + base + i) : 0ull;
+      k[i] = 1;
+      cand[i] = 0;
+    }
+    bool more = n >= 1;
+    while (more) {
+      uint64_t key[kQ];
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) key[i] = k[i] <= n ? __ldg(ek + k[i]) : 0ull;
+      more = false;
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) {
+        if (k[i] <= n) {
+          const bool right = key[i] < x[i];
+          if (!right) cand[i] = k[i];
+          k[i] = 2 * k[i] + (right ? 1 : 0);
+          more |= k[i] <= n;
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      if (base + i >= nq) break;
+      const bool hit = cand[i] != 0 && __ldg(ek + cand[i]) == x[i];
+      const int64_t v = hit ? int64_t(__ldg(ev + cand[i])) : absent;
+      if (out) {
+        if (kI64) static_cast<int64_t*>(out)[base + i] = v;
+        else static_cast<int32_t*>(out)[base + i] = int32_t(v);
+      }
+      if (found) found[base + i] = uint8_t(hit);
+    }
+  }
+}
+
 __global__ void k_widen_i32(const int32_t* __restrict__ in, uint64_t n, uint64_t* __restrict__ out) {
   const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
   for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride)
     out[i] = uint64_t(int64_t(in[i]));
-}
-
-cudaError_t scan(uint32_t* data, uint64_t n, uint32_t* sums, cudaStream_t st) {
-  const uint32_t nb = uint32_t((n + kScanItems - 1) / kScanItems);
-  k_sum_blocks<<<nb, kScanThreads, 0, st>>>(data, n, sums);
-  k_scan_block_sums<<<1, 1024, 0, st>>>(sums, nb);
-  k_scan_apply<<<nb, kScanThreads, 0, st>>>(data, n, sums);
-  return cudaGetLastError();
 }
 
 }  // namespace
@@ -212,7 +223,8 @@ cudaError_t scan(uint32_t* data, uint64_t n, uint32_t* sums, cudaStream_t st) {
 size_t sort_scratch_bytes(uint64_t n) {
   const uint64_t tiles = (n + kSortTile - 1) / kSortTile;
   const uint64_t hist = 256 * tiles;
-  return 2 * 8 * n + 4 * hist + 4 * (hist / kScanItems + 2) + 1024;
+  const size_t bytes = 2 * 8 * n + 4 * hist + 4 * scan_sum_words(hist) + 1024;
+  return (bytes + 255) & ~size_t(255);  // buffers placed after the scratch stay aligned
 }
 
 // Sort (keys, vals) ascending by key into (kout, vout); vals are 64-bit
@@ -233,14 +245,14 @@ cudaError_t launch_sort_pairs(const uint64_t* keys, const uint64_t* vals, uint64
     uint64_t* ov = (pass & 1) ? vout : tv;
     const uint32_t shift = 8 * pass;
     k_sort_count<<<tiles, kSortThreads, 0, st>>>(ik, n, shift, tiles, hist);
-    cudaError_t e = scan(hist, 256ull * tiles, sums, st);
+    cudaError_t e = scan_exclusive<uint32_t>(hist, 256ull * tiles, sums, st);
     if (e != cudaSuccess) return e;
     k_sort_scatter<<<tiles, kSortThreads, 0, st>>>(ik, iv, ok, ov, n, shift, tiles, hist);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     ik = ok;
     iv = ov;
   }
-  note_launches(8 * 5);
+  note_launches(8 * 2);  // the scans count their own
   return cudaSuccess;
 }
 
@@ -260,6 +272,33 @@ cudaError_t launch_sorted_search(const uint64_t* keys, const uint64_t* vals, uin
   if (blocks > cap) blocks = cap;
   if (out_i64) k_search<true><<<unsigned(blocks), 256, 0, st>>>(keys, vals, n, q, nq, out, found, absent);
   else k_search<false><<<unsigned(blocks), 256, 0, st>>>(keys, vals, n, q, nq, out, found, absent);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace fks
+
+namespace fks {
+
+cudaError_t launch_eytzinger_layout(const uint64_t* sk, const uint64_t* sv, uint64_t n, uint64_t* ek, uint64_t* ev,
+                                    int sms, cudaStream_t st) {
+  uint64_t blocks = (n + 1 + 255) / 256;
+  const uint64_t cap = uint64_t(sms) * 16;
+  if (blocks > cap) blocks = cap;
+  k_eytz_gather<<<unsigned(blocks), 256, 0, st>>>(sk, sv, n, ek, ev);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eytzinger_search(const uint64_t* ek, const uint64_t* ev, uint64_t n, const uint64_t* q, uint64_t nq,
+                                    void* out, int out_i64, uint8_t* found, int64_t absent, int sms, cudaStream_t st) {
+  if (nq == 0) return cudaSuccess;
+  constexpr int kQ = 4;
+  uint64_t blocks = (nq + 256 * kQ - 1) / (256 * kQ);
+  const uint64_t cap = uint64_t(sms) * 8;
+  if (blocks > cap) blocks = cap;
+  if (out_i64) k_eytz_search<kQ, true><<<unsigned(blocks), 256, 0, st>>>(ek, ev, n, q, nq, out, found, absent);
+  else k_eytz_search<kQ, false><<<unsigned(blocks), 256, 0, st>>>(ek, ev, n, q, nq, out, found, absent);
   note_launches(1);
   return cudaGetLastError();
 }

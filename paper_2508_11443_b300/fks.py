@@ -94,6 +94,8 @@ def lib():
         L.fks_last_error.restype = ctypes.c_char_p
         L.fks_sortmap_build.argtypes = [vp, vp, ctypes.c_int, u64, vp, vp, ctypes.POINTER(vp)]
         L.fks_sortmap_build.restype = st
+        L.fks_eytzmap_build.argtypes = [vp, vp, ctypes.c_int, u64, vp, vp, ctypes.POINTER(vp)]
+        L.fks_eytzmap_build.restype = st
         L.fks_sortmap_lookup.argtypes = [vp, vp, u64, vp, vp, i64, vp]
         L.fks_sortmap_lookup.restype = st
         L.fks_sortmap_export.argtypes = [vp, vp, vp, vp]
@@ -293,6 +295,13 @@ class SortMap:
 def fks_sortmap_build(keys, vals, stream=None) -> SortMap:
     h = ctypes.c_void_p()
     _check(lib().fks_sortmap_build(_ptr(keys), _ptr(vals), _val_type(vals), keys.numel(), None,
+                                   _stream(stream), ctypes.byref(h)))
+    return SortMap(h.value, keys.numel())
+
+
+def fks_eytzmap_build(keys, vals, stream=None) -> SortMap:
+    h = ctypes.c_void_p()
+    _check(lib().fks_eytzmap_build(_ptr(keys), _ptr(vals), _val_type(vals), keys.numel(), None,
                                    _stream(stream), ctypes.byref(h)))
     return SortMap(h.value, keys.numel())
 

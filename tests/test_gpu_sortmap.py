@@ -63,3 +63,41 @@ def test_sort_is_stable_and_int32_values(F):
     torch.cuda.synchronize()
     _, _, eo, _ = expected(keys, vals.astype(np.int64), keys[:100], -1)
     assert np.array_equal(out.cpu().numpy().astype(np.int64), eo)
+
+
+# ------------------------------------------------------------------ Eytzinger layout (Sec. 3.4)
+@pytest.mark.parametrize("n", [1, 2, 3, 7, 8, 1023, 1024, 2049, 100000, (1 << 20) + 3, (1 << 22) + 12345])
+def test_eytzinger_layout_and_search(F, n):
+    """The device layout equals the oracle's Eytzinger layout of the sorted
+    pairs; lookups equal the oracle's Eytzinger search and binary search."""
+    import torch
+    import oracle as O
+    w = W.u64_workload(n, 2 * n + 2, 0.5, seed=n + 9)
+    m = F.fks_eytzmap_build(dev(w.keys), dev(w.vals))
+    gk, gv = F.fks_sortmap_export(m)
+    sk, sv, eo, ef = expected(w.keys, w.vals, w.queries, -4)
+    ok, ov = O.eytzinger_layout(sk, sv)
+    assert np.array_equal(gk, ok[1:]) and np.array_equal(gv, ov[1:])
+    q = np.concatenate([w.queries, [0, 2**64 - 1], sk[:1], sk[-1:]]).astype(np.uint64)
+    out = torch.empty(q.size, dtype=torch.int64, device="cuda")
+    found = torch.empty(q.size, dtype=torch.uint8, device="cuda")
+    F.fks_sortmap_lookup(m, dev(q), out, found, -4)
+    torch.cuda.synchronize()
+    _, _, eo, ef = expected(w.keys, w.vals, q, -4)
+    assert np.array_equal(out.cpu().numpy(), eo) and np.array_equal(found.cpu().numpy(), ef)
+    for x in q[:: max(1, q.size // 500)].tolist():  # the oracle's own search on a sample
+        k = O.eytzinger_search(ok, x)
+        i = int(np.searchsorted(sk, x))
+        assert (k != 0) == (i < sk.size and sk[min(i, sk.size - 1)] == x)
+
+
+def test_eytzinger_int32_values(F):
+    import torch
+    w = W.u64_workload(5000, 3000, 0.5, seed=4)
+    vals = np.arange(5000, dtype=np.int32) - 2500
+    m = F.fks_eytzmap_build(dev(w.keys), dev(vals))
+    out = torch.empty(3000, dtype=torch.int32, device="cuda")
+    F.fks_sortmap_lookup(m, dev(w.queries), out, None, -7)
+    torch.cuda.synchronize()
+    _, _, eo, _ = expected(w.keys, vals.astype(np.int64), w.queries, -7)
+    assert np.array_equal(out.cpu().numpy().astype(np.int64), eo)
