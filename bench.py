@@ -73,10 +73,12 @@ def load_traffic():
 
 # source files each kernel is compiled from (digest ties ncu counters to code)
 KERNEL_SOURCES = {
-    "k_lookup_u64": ["fks_device.cuh", "fks_internal.cuh", "fks_lookup.cu"],
-    "k_part_build": ["fks_device.cuh", "fks_internal.cuh", "fks_build.cu"],
-    "k_partition_scatter": ["fks_device.cuh", "fks_internal.cuh", "fks_build.cu"],
-    "k_partition_count": ["fks_device.cuh", "fks_internal.cuh", "fks_build.cu"],
+    "k_lookup_u64": ["fks_device.cuh", "fks_internal.cuh", "fks_strings.cuh", "fks_lookup.cu"],
+    "k_part_build": ["fks_device.cuh", "fks_internal.cuh", "fks_strings.cuh", "fks_build.cu"],
+    "k_partition_scatter": ["fks_device.cuh", "fks_internal.cuh", "fks_strings.cuh", "fks_build.cu"],
+    "k_partition_count": ["fks_device.cuh", "fks_internal.cuh", "fks_strings.cuh", "fks_build.cu"],
+    "k_scatterA": ["fks_device.cuh", "fks_internal.cuh", "fks_split.cu"],
+    "k_scatterB": ["fks_device.cuh", "fks_internal.cuh", "fks_split.cu"],
 }
 
 

@@ -50,6 +50,9 @@ struct Elem {
   uint32_t gp;
 };
 
+// Two halves so that a thread issues the loads of all its elements before
+// it uses any of them: load_elem reads (the partition field holds the map),
+// finish_elem hashes and packs.
 template <bool kStr>
 __device__ __forceinline__ Elem<kStr> load_elem(const PassDev& p, const uint64_t* seg, uint64_t e) {
   const uint32_t j = p.m == 1 ? 0u : seg_of(seg, p.m, e);
@@ -57,9 +60,9 @@ __device__ __forceinline__ Elem<kStr> load_elem(const PassDev& p, const uint64_t
   const uint64_t in = M.key_begin + (e - M.pass_begin);
   Elem<kStr> x;
   x.key = __ldcs(reinterpret_cast<const unsigned long long*>(p.hkeys) + in);
-  x.gp = M.part_begin + (reduce32(hash32(M.c1, x.key), M.nb) >> p.logB);
   const int64_t v = p.vals_i64 ? __ldcs(static_cast<const long long*>(p.vals) + in)
                                : int64_t(__ldcs(static_cast<const int*>(p.vals) + in));
+  x.gp = j;
   if (!kStr) {
     x.p0 = uint64_t(v);
     x.p1 = 0;
@@ -73,10 +76,19 @@ __device__ __forceinline__ Elem<kStr> load_elem(const PassDev& p, const uint64_t
   return x;
 }
 
-__device__ __forceinline__ uint32_t gp_only(const PassDev& p, const uint64_t* seg, uint64_t e) {
-  const uint32_t j = p.m == 1 ? 0u : seg_of(seg, p.m, e);
+template <bool kStr>
+__device__ __forceinline__ void finish_elem(const PassDev& p, Elem<kStr>& x) {
+  const MapDev& M = p.maps[x.gp];
+  x.gp = M.part_begin + (reduce32(hash32(M.c1, x.key), M.nb) >> p.logB);
+}
+
+__device__ __forceinline__ uint64_t key_only(const PassDev& p, const uint64_t* seg, uint64_t e, uint32_t* j) {
+  *j = p.m == 1 ? 0u : seg_of(seg, p.m, e);
+  const MapDev& M = p.maps[*j];
+  return __ldcs(reinterpret_cast<const unsigned long long*>(p.hkeys) + M.key_begin + (e - M.pass_begin));
+}
+__device__ __forceinline__ uint32_t gp_of(const PassDev& p, uint32_t j, uint64_t k) {
   const MapDev& M = p.maps[j];
-  const uint64_t k = __ldcs(reinterpret_cast<const unsigned long long*>(p.hkeys) + M.key_begin + (e - M.pass_begin));
   return M.part_begin + (reduce32(hash32(M.c1, k), M.nb) >> p.logB);
 }
 
@@ -111,7 +123,19 @@ __global__ void __launch_bounds__(kSplitThreads) k_countA(PassDev p, SplitDev s)
   __syncthreads();
   const uint32_t tile = blockIdx.x;
   const uint64_t e0 = uint64_t(tile) * kTile, e1 = min(p.total, e0 + kTile);
-  for (uint64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) atomicAdd(hist + (gp_only(p, seg, e) >> s.shiftB), 1u);
+  constexpr uint32_t kPer = kTile / kSplitThreads;
+  uint64_t k[kPer];
+  uint32_t jm[kPer];
+#pragma unroll
+  for (uint32_t u = 0; u < kPer; ++u) {  // all loads first
+    const uint64_t e = e0 + threadIdx.x + u * kSplitThreads;
+    k[u] = e < e1 ? key_only(p, seg, e, &jm[u]) : 0ull;
+  }
+#pragma unroll
+  for (uint32_t u = 0; u < kPer; ++u) {
+    const uint64_t e = e0 + threadIdx.x + u * kSplitThreads;
+    if (e < e1) atomicAdd(hist + (gp_of(p, jm[u], k[u]) >> s.shiftB), 1u);
+  }
   __syncthreads();
   for (uint32_t a = threadIdx.x; a < s.binsA; a += blockDim.x) s.histA[uint64_t(a) * s.tilesA + tile] = hist[a];
 }
@@ -142,10 +166,15 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_scatterA(PassDev p, SplitD
   Elem<kStr> x[kPer];
   uint32_t rank[kPer];
 #pragma unroll
+  for (uint32_t u = 0; u < kPer; ++u) {  // all loads first
+    const uint32_t i = threadIdx.x + u * kSplitThreads;
+    if (i < cnt) x[u] = load_elem<kStr>(p, seg, e0 + i);
+  }
+#pragma unroll
   for (uint32_t u = 0; u < kPer; ++u) {
     const uint32_t i = threadIdx.x + u * kSplitThreads;
     if (i < cnt) {
-      x[u] = load_elem<kStr>(p, seg, e0 + i);
+      finish_elem<kStr>(p, x[u]);
       rank[u] = atomicAdd(cur + (x[u].gp >> s.shiftB), 1u);
     }
   }
@@ -243,7 +272,16 @@ __global__ void __launch_bounds__(kSplitThreads) k_countB(PassDev p, SplitDev s)
   for (uint32_t i = threadIdx.x; i < s.binsB; i += blockDim.x) hist[i] = 0;
   __syncthreads();
   const uint32_t mask = s.binsB - 1;
-  for (uint64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) atomicAdd(hist + (__ldcs(s.gpA + e) & mask), 1u);
+  constexpr uint32_t kPer = kTile / kSplitThreads;
+  uint32_t g[kPer];
+#pragma unroll
+  for (uint32_t u = 0; u < kPer; ++u) {  // all loads first
+    const uint64_t e = e0 + threadIdx.x + u * kSplitThreads;
+    g[u] = e < e1 ? __ldcs(s.gpA + e) : 0u;
+  }
+#pragma unroll
+  for (uint32_t u = 0; u < kPer; ++u)
+    if (e0 + threadIdx.x + u * kSplitThreads < e1) atomicAdd(hist + (g[u] & mask), 1u);
   __syncthreads();
   for (uint32_t d = threadIdx.x; d < s.binsB; d += blockDim.x) s.histB[histB_index(s, s.tstartB, a, d, t)] = hist[d];
   (void)p;
@@ -271,7 +309,7 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_scatterB(PassDev p, SplitD
   uint64_t k[kPer], q0[kPer], q1[kPer];
   uint32_t d[kPer], rank[kPer];
 #pragma unroll
-  for (uint32_t u = 0; u < kPer; ++u) {
+  for (uint32_t u = 0; u < kPer; ++u) {  // all loads first
     const uint32_t i = threadIdx.x + u * kSplitThreads;
     if (i < cnt) {
       const uint64_t e = e0 + i;
@@ -279,9 +317,11 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_scatterB(PassDev p, SplitD
       q0[u] = __ldcs(reinterpret_cast<const unsigned long long*>(s.payA) + PW * e);
       q1[u] = kStr ? __ldcs(reinterpret_cast<const unsigned long long*>(s.payA) + PW * e + 1) : 0ull;
       d[u] = __ldcs(s.gpA + e) & mask;
-      rank[u] = atomicAdd(cur + d[u], 1u);
     }
   }
+#pragma unroll
+  for (uint32_t u = 0; u < kPer; ++u)
+    if (threadIdx.x + u * kSplitThreads < cnt) rank[u] = atomicAdd(cur + d[u], 1u);
   __syncthreads();
   {
     constexpr uint32_t kPerBin = kMaxBins / kSplitThreads;
