@@ -255,7 +255,7 @@ static bool read_opts(const fks_build_opts* o, Opts* out) {
 // Buckets of up to this many keys are searched by a single thread, larger
 // ones by packed warp segments (measured on 2^26-key builds: 3 for small
 // buckets; with 8 or 16 keys per bucket every bucket goes to a segment).
-static uint32_t thread_search_max(uint32_t lambda) { return lambda <= 4 ? 3u : 1u; }
+static uint32_t thread_search_max(uint32_t lambda) { return lambda <= 4 ? kThreadSearchMax : 1u; }
 
 // Slot offsets are 32-bit descriptor fields: bound * n must stay below 2^32.
 static bool sizes_fit(const Opts& o, uint64_t n) { return uint64_t(o.bound) * n <= 0xFFFFFFFFull; }

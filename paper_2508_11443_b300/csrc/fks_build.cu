@@ -231,6 +231,17 @@ __global__ void __launch_bounds__(1024) k_scan_parts(PassDev p) {
 }
 
 // -------------------------------------------------------------- partition CTA
+// Search classes of a bucket of s >= 2 keys: 0 = one thread (s <= thr), 1..5 =
+// a segment of 2^cls lanes (s <= 32), 6 = the whole CTA.
+constexpr uint32_t kClasses = 7;
+// With at most kCap keys a class of buckets of >= s_min keys has at most
+// kCap / s_min entries: fixed list regions in the work array.
+__host__ __device__ constexpr uint32_t class_region(uint32_t c) {
+  return c == 0 ? 0u : c == 1 ? 1024u : c == 2 ? 2048u : c == 3 ? 2730u : c == 4 ? 3139u : c == 5 ? 3366u : 3486u;
+}
+constexpr uint32_t kWorkEntries = 3548;  // class_region(6) + kCap / 33
+static_assert(kCap == 2048, "class regions assume 2048 keys per partition");
+
 __host__ __device__ constexpr uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 
 // Shared memory of a partition CTA.  raw*: the partition's staged keys and
@@ -249,8 +260,8 @@ struct Smem {
   static constexpr uint32_t kGst = kCnt + kB * 4;
   static constexpr uint32_t kSoff = kGst + (kB + 4) * 4;
   static constexpr uint32_t kAtt = kSoff + kB * 4;
-  static constexpr uint32_t kWork = align16(kAtt + kB * 2);  // buckets that need a search
-  static constexpr uint32_t kBytes = align16(kWork + kB * 2);
+  static constexpr uint32_t kWork = align16(kAtt + kB * 2);  // class lists of the buckets to search
+  static constexpr uint32_t kBytes = align16(kWork + kWorkEntries * 2);
 };
 
 struct PartCtl {
@@ -493,47 +504,6 @@ __device__ __forceinline__ bool same_member(const PassDev& p, const uint64_t* gp
 
 enum { kSearchDup = -1, kSearchNext = -2 };
 
-// make_2 for one bucket of 2 <= s <= 8 keys by one thread: the first attempt
-// whose s hashes into s^2 <= 64 slots are pairwise distinct; the slot
-// occupancy is a 64-bit register bitmap, returned with the constants.
-template <int PW>
-__device__ int search_thread(const PassDev& p, const uint64_t* k, const uint64_t* gpay,
-                             uint32_t g0, uint32_t s, uint64_t seed, uint32_t round, uint32_t b,
-                             HashConsts* found, uint64_t* occupied) {
-  const uint32_t m = s * s;
-  for (uint32_t a = 0; a < p.cfg.attempt_cap; ++a) {
-    if (a == kDupCheckAttempt) {
-      bool eq = false, dup = false;
-      for (uint32_t x = 0; x < s; ++x)
-        for (uint32_t y = x + 1; y < s; ++y)
-          if (k[x] == k[y]) {
-            eq = true;
-            dup |= same_member<PW>(p, gpay, g0 + x, g0 + y);
-          }
-      if (dup) return kSearchDup;
-      if (eq) return kSearchNext;
-    }
-    const HashConsts c = derive(seed, round, b, a);
-    bool col = false;
-    uint64_t bits = 0;
-#pragma unroll
-    for (uint32_t x = 0; x < kThreadSearchMax; ++x) {
-      if (x < s) {
-        const uint64_t bit = 1ull << reduce32(hash32(c, k[x]), m);
-        col |= (bits & bit) != 0;
-        bits |= bit;
-      }
-    }
-    if (a < p.cfg.reject) continue;
-    if (!col) {
-      *found = c;
-      *occupied = bits;
-      return int(a);
-    }
-  }
-  return kSearchNext;
-}
-
 template <int PW>
 __device__ __forceinline__ void write_slot(const PassDev& p, uint64_t idx, uint64_t key,
                                            const uint64_t* pay, bool fill) {
@@ -546,30 +516,52 @@ __device__ __forceinline__ void write_slot(const PassDev& p, uint64_t idx, uint6
   }
 }
 
-// Place one searched bucket (thread level, s <= 8).  owner mode: record
-// member / filler indices in the shared slot image; else write the slots
-// directly.  `bits` marks the occupied slots of the bucket's range.
+// make_2 + placement for a bucket of 2 or 3 keys by one thread: the first
+// attempt whose slot indices in the s^2 <= 9 slots are pairwise distinct,
+// then every slot of the range written once (member, or the filler: the
+// lowest occupied slot's key with value -1).  Returns the attempt, or
+// kSearchDup / kSearchNext.
 template <int PW>
-__device__ void place_thread(const PassDev& p, const uint64_t* k, const uint64_t* gpay,
-                             uint32_t g0, uint32_t s, const HashConsts& c, uint64_t bits, uint16_t* owner,
-                             uint32_t so, uint64_t slot0, bool owner_mode) {
+__device__ int search_place_small(const PassDev& p, const uint64_t* gkey, const uint64_t* gpay, uint32_t g0,
+                                  uint32_t s, uint64_t seed, uint32_t round, uint32_t b, uint16_t* owner,
+                                  uint32_t so, uint64_t slot0, bool owner_mode) {
   const uint32_t m = s * s;
-  const uint32_t jmin = uint32_t(__ffsll(static_cast<long long>(bits)) - 1);
-  uint32_t xmin = 0;
-  for (uint32_t x = 0; x < s; ++x) {
-    const uint32_t jj = reduce32(hash32(c, k[x]), m);
-    if (jj == jmin) xmin = x;
-    if (owner_mode) owner[so + jj] = uint16_t(g0 + x);
-    else write_slot<PW>(p, slot0 + jj, k[x], gpay + PW * (g0 + x), false);
+  const bool three = s == 3;
+  const uint64_t k0 = gkey[g0], k1 = gkey[g0 + 1], k2 = three ? gkey[g0 + 2] : 0ull;
+  uint32_t j0 = 0, j1 = 0, j2 = 0;
+  int found = kSearchNext;
+  for (uint32_t a = 0; a < p.cfg.attempt_cap; ++a) {
+    if (a == kDupCheckAttempt) {
+      const bool e01 = k0 == k1, e02 = three && k0 == k2, e12 = three && k1 == k2;
+      if (e01 || e02 || e12) {  // every equal pair
+        bool dup = e01 && same_member<PW>(p, gpay, g0, g0 + 1);
+        dup |= e02 && same_member<PW>(p, gpay, g0, g0 + 2);
+        dup |= e12 && same_member<PW>(p, gpay, g0 + 1, g0 + 2);
+        return dup ? kSearchDup : kSearchNext;
+      }
+    }
+    const HashConsts c = derive(seed, round, b, a);
+    j0 = reduce32(hash32(c, k0), m);
+    j1 = reduce32(hash32(c, k1), m);
+    j2 = three ? reduce32(hash32(c, k2), m) : 0xFFFFu;
+    const bool col = j0 == j1 || (three && (j0 == j2 || j1 == j2));
+    if (a < p.cfg.reject) continue;
+    if (!col) {
+      found = int(a);
+      break;
+    }
   }
-  // the rest of the range: the lowest occupied slot's key, value -1
-  uint64_t empty = ~bits & (m == 64 ? ~0ull : ((1ull << m) - 1));
-  while (empty) {
-    const uint32_t t = uint32_t(__ffsll(static_cast<long long>(empty)) - 1);
-    empty &= empty - 1;
-    if (owner_mode) owner[so + t] = uint16_t(kOwnerFill | (g0 + xmin));
-    else write_slot<PW>(p, slot0 + t, k[xmin], gpay + PW * (g0 + xmin), true);
+  if (found < 0) return found;
+  const uint32_t jmin = min(j0, min(j1, j2));
+  const uint32_t xmin = jmin == j0 ? 0u : (jmin == j1 ? 1u : 2u);
+  for (uint32_t t = 0; t < m; ++t) {
+    const uint32_t x = t == j0 ? 0u : (t == j1 ? 1u : (t == j2 ? 2u : 3u));
+    const bool fill = x == 3u;
+    const uint32_t src = g0 + (fill ? xmin : x);
+    if (owner_mode) owner[so + t] = uint16_t(fill ? (kOwnerFill | src) : src);
+    else write_slot<PW>(p, slot0 + t, gkey[src], gpay + PW * src, fill);
   }
+  return found;
 }
 
 // make_2 + placement for up to 32 / G buckets of 2 <= s <= G keys by one warp
@@ -744,7 +736,6 @@ __device__ __noinline__ void search_place_cta(const PassDev& p, const uint64_t* 
 
 // Search classes of a bucket of s >= 2 keys: 0 = one thread (s <= thr), 1..5 =
 // a segment of 2^cls lanes (s <= 32), 6 = the whole CTA.
-constexpr uint32_t kClasses = 7;
 __device__ __forceinline__ uint32_t search_class(uint32_t s, uint32_t thr) {
   if (s <= thr) return 0;
   if (s > 32) return 6;
@@ -754,11 +745,13 @@ __device__ __forceinline__ uint32_t search_class(uint32_t s, uint32_t thr) {
 // Level-two search (make_2) of every bucket of a grouped partition, then the
 // placement of its keys: slot image in shared memory (owner mode) or direct
 // writes.  Empty and single-key buckets need no search (attempt 0); the
-// others are listed by class (counted, then placed, one shared atomic per
-// warp and class): small buckets are searched by single threads from the
-// low warps, mid-size ones in packed warp segments from the high warps (no
-// barrier between the two), buckets above 32 keys by the whole CTA.
-template <int PW>
+// others are listed by class, one shared atomic per warp and class -- into
+// fixed regions in one pass when the partition holds at most kCap keys
+// (kFixed), else counted first and placed in a second pass.  Small buckets
+// are searched by single threads from the low warps, mid-size ones in
+// packed warp segments from the high warps (no barrier between the two),
+// buckets above 32 keys by the whole CTA.
+template <int PW, bool kFixed>
 __device__ void search_partition(const PassDev& p, const MapRegs& M, uint32_t j, uint32_t b0,
                                  uint32_t nb, uint64_t slot_part, bool owner_mode,
                                  const uint64_t* gkey, const uint64_t* gpay, uint16_t* owner,
@@ -766,7 +759,8 @@ __device__ void search_partition(const PassDev& p, const MapRegs& M, uint32_t j,
                                  uint16_t* work, PartCtl& ctl) {
   const uint32_t thr = p.cfg.thread_max;
   const uint32_t lane = lane_id();
-  // pass 1: singletons placed, classes counted
+  if (kFixed && threadIdx.x < kClasses) ctl.cbase[threadIdx.x] = class_region(threadIdx.x);
+  // pass 1: singletons placed, classes counted (kFixed: listed)
   for (uint32_t lb0 = threadIdx.x & ~31u; lb0 < nb; lb0 += kPartThreads) {
     const uint32_t lb = lb0 + lane;
     uint32_t g0 = 0, s = 0;
@@ -781,10 +775,18 @@ __device__ void search_partition(const PassDev& p, const MapRegs& M, uint32_t j,
     }
     const uint32_t c = (lb < nb && s > 1) ? search_class(s, thr) : kClasses;
     const uint32_t peers = __match_any_sync(0xFFFFFFFFu, c);
-    if (c < kClasses && lane == uint32_t(__ffs(peers) - 1)) atomicAdd(&ctl.ccnt[c], uint32_t(__popc(peers)));
+    const uint32_t leader = uint32_t(__ffs(peers) - 1);
+    if (kFixed) {
+      uint32_t base = 0;
+      if (c < kClasses && lane == leader) base = atomicAdd(&ctl.ccnt[c], uint32_t(__popc(peers)));
+      base = __shfl_sync(0xFFFFFFFFu, base, leader);
+      if (c < kClasses) work[class_region(c) + base + __popc(peers & lanemask_lt())] = uint16_t(lb);
+    } else if (c < kClasses && lane == leader) {
+      atomicAdd(&ctl.ccnt[c], uint32_t(__popc(peers)));
+    }
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (!kFixed && threadIdx.x == 0) {
     uint32_t run = 0;
     for (uint32_t c = 0; c < kClasses; ++c) {
       ctl.cbase[c] = run;
@@ -792,9 +794,9 @@ __device__ void search_partition(const PassDev& p, const MapRegs& M, uint32_t j,
       run += ctl.ccnt[c];
     }
   }
-  __syncthreads();
+  if (!kFixed) __syncthreads();
   // pass 2: the class lists
-  for (uint32_t lb0 = threadIdx.x & ~31u; lb0 < nb; lb0 += kPartThreads) {
+  for (uint32_t lb0 = threadIdx.x & ~31u; !kFixed && lb0 < nb; lb0 += kPartThreads) {
     const uint32_t lb = lb0 + lane;
     uint32_t s = 0;
     if (lb < nb) s = gst[lb + 1] - gst[lb];
@@ -806,22 +808,20 @@ __device__ void search_partition(const PassDev& p, const MapRegs& M, uint32_t j,
     base = __shfl_sync(0xFFFFFFFFu, base, leader);
     if (c < kClasses) work[base + __popc(peers & lanemask_lt())] = uint16_t(lb);
   }
-  __syncthreads();
+  if (!kFixed) __syncthreads();
   uint32_t my_max = 0;
   uint64_t my_sum = 0;
   // single-thread searches, from thread 0 up
   const uint32_t n0 = ctl.ccnt[0];
   for (uint32_t w = threadIdx.x; w < n0; w += kPartThreads) {
-    const uint32_t lb = work[w];
+    const uint32_t lb = work[ctl.cbase[0] + w];
     const uint32_t g0 = gst[lb], s = gst[lb + 1] - g0;
-    HashConsts c;
-    uint64_t bits = 0;
-    const int a = search_thread<PW>(p, gkey + g0, gpay, g0, s, M.seed, M.round, b0 + lb, &c, &bits);
+    const int a = search_place_small<PW>(p, gkey, gpay, g0, s, M.seed, M.round, b0 + lb, owner, soff[lb],
+                                         slot_part + soff[lb], owner_mode);
     if (a >= 0) {
       att[lb] = uint16_t(a);
       my_max = max(my_max, uint32_t(a));
       my_sum += uint64_t(a);
-      place_thread<PW>(p, gkey + g0, gpay, g0, s, c, bits, owner, soff[lb], slot_part + soff[lb], owner_mode);
     } else {
       atomicExch(a == kSearchDup ? &p.status[j].dup : &p.status[j].next_round, 1u);
       ctl.failed = 1;
@@ -1033,8 +1033,8 @@ __global__ void __launch_bounds__(kPartThreads, PW == 1 ? 2 : 1) k_part_build(Pa
       __syncthreads();
       continue;
     }
-    search_partition<PW>(p, M, j, b0, nb, M.slot_base + ctl.excl, owner_mode, gkey, gpay, owner, gst,
-                         soff, att, work, ctl);
+    search_partition<PW, true>(p, M, j, b0, nb, M.slot_base + ctl.excl, owner_mode, gkey, gpay, owner, gst,
+                               soff, att, work, ctl);
     if (!early) {
       if (t < 32) finish_prefix(p, M, gp, j, Sp, ctl);
       __syncthreads();
@@ -1100,8 +1100,8 @@ __global__ void __launch_bounds__(kPartThreads, 1) k_part_overflow(PassDev p) {
     for (int w = 0; w < PW; ++w) gpay[PW * pos + w] = p.stage_pay[PW * e + w];
   }
   __syncthreads();
-  search_partition<PW>(p, M, j, b0, nb, M.slot_base + excl, owner_mode, gkey, gpay, owner, gst, soff,
-                       att, work, ctl);
+  search_partition<PW, false>(p, M, j, b0, nb, M.slot_base + excl, owner_mode, gkey, gpay, owner, gst, soff,
+                              att, work, ctl);
   if (!ctl.failed)
     write_partition<PW>(p, M, b0, nb, excl, owner_mode, gkey, gpay, owner, gst, soff, att, Sp);
   if (t == 0) flush_stats(p, j, ctl);

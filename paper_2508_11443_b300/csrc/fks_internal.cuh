@@ -33,7 +33,7 @@ __host__ __device__ constexpr uint64_t level1_buckets(uint64_t n, uint32_t lambd
   return (n + lambda - 1) / lambda;
 }
 constexpr int kPartThreads = 512;      // threads of a partition CTA
-constexpr uint32_t kThreadSearchMax = 8;  // largest bucket a single thread can search (64-bit bitmap)
+constexpr uint32_t kThreadSearchMax = 3;  // largest bucket a single thread searches
 constexpr uint16_t kOwnerEmpty = 0xFFFF;
 constexpr uint16_t kOwnerFill = 0x8000;
 
