@@ -270,6 +270,7 @@ struct PartCtl {
   uint32_t nwork;
   uint32_t ccnt[8], cbase[8], ccur[8];  // search classes: list sizes, starts, cursors
   uint32_t next_gp, next_issued, abort;
+  uint64_t next_e0, next_e1;  // staged range of partition next_gp
   uint64_t excl, Spart, attsum;
   unsigned long long fillmin;  // (slot << 32) | member of a CTA-searched bucket
   uint32_t wsum[kPartThreads / 32];
@@ -329,13 +330,16 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// Thread 0: start the copy of partition gp's staged range into raw*.
-// Returns 1 if a copy was issued (the caller waits on the mbarrier).
+// One thread: start the copy of partition gp's staged range into raw* and
+// record the range in *r0, *r1.  Returns 1 if a copy was issued (the caller
+// waits on the mbarrier).
 template <int PW>
 __device__ uint32_t issue_stage(const PassDev& p, uint32_t gp, uint64_t* raw_key, uint64_t* raw_pay,
-                                uint64_t* bar) {
+                                uint64_t* bar, uint64_t* r0, uint64_t* r1) {
   if (gp >= p.P) return 0;
   const uint64_t e0 = p.part_start[gp], e1 = p.part_start[gp + 1];
+  *r0 = e0;
+  *r1 = e1;
   if (e1 == e0 || e1 - e0 > kCap) return 0;
   const uint64_t a0 = e0 & ~1ull;                 // 16-byte aligned start of the key copy
   const uint32_t nk = uint32_t((e1 - a0 + 1) & ~1ull);  // even element count
@@ -473,13 +477,13 @@ __device__ uint64_t resolve_prefix(const PassDev& p, uint32_t gp, uint32_t first
   return excl;
 }
 
-// Warp 0: resolve the prefix and record the partition's outcome in ctl and
-// in the map's status.
+// One warp: resolve the prefix and record the partition's outcome in ctl
+// and in the map's status.
 __device__ void finish_prefix(const PassDev& p, const MapRegs& M, uint32_t gp, uint32_t j, uint64_t Sp,
                               PartCtl& ctl) {
   bool to = false;
   const uint64_t excl = resolve_prefix(p, gp, M.part_begin, Sp, &to);
-  if (threadIdx.x == 0) {
+  if (lane_id() == 0) {
     const uint64_t incl = excl + Sp;
     ctl.excl = excl;
     ctl.skip = (to || incl > M.slot_cap) ? 1u : 0u;
@@ -751,12 +755,15 @@ __device__ __forceinline__ uint32_t search_class(uint32_t s, uint32_t thr) {
 // are searched by single threads from the low warps, mid-size ones in
 // packed warp segments from the high warps (no barrier between the two),
 // buckets above 32 keys by the whole CTA.
+//
+// resolve: the slot prefix of partition gp (size Sp) is resolved here, by
+// the first warp without single-thread searches, while the others search.
 template <int PW, bool kFixed>
 __device__ void search_partition(const PassDev& p, const MapRegs& M, uint32_t j, uint32_t b0,
                                  uint32_t nb, uint64_t slot_part, bool owner_mode,
                                  const uint64_t* gkey, const uint64_t* gpay, uint16_t* owner,
                                  const uint32_t* gst, const uint32_t* soff, uint16_t* att,
-                                 uint16_t* work, PartCtl& ctl) {
+                                 uint16_t* work, PartCtl& ctl, bool resolve, uint32_t gp, uint64_t Sp) {
   const uint32_t thr = p.cfg.thread_max;
   const uint32_t lane = lane_id();
   if (kFixed && threadIdx.x < kClasses) ctl.cbase[threadIdx.x] = class_region(threadIdx.x);
@@ -813,6 +820,8 @@ __device__ void search_partition(const PassDev& p, const MapRegs& M, uint32_t j,
   uint64_t my_sum = 0;
   // single-thread searches, from thread 0 up
   const uint32_t n0 = ctl.ccnt[0];
+  if (resolve && (threadIdx.x >> 5) == min(kPartThreads / 32 - 1, (n0 + 31) / 32))
+    finish_prefix(p, M, gp, j, Sp, ctl);
   for (uint32_t w = threadIdx.x; w < n0; w += kPartThreads) {
     const uint32_t lb = work[ctl.cbase[0] + w];
     const uint32_t g0 = gst[lb], s = gst[lb + 1] - g0;
@@ -928,18 +937,22 @@ __global__ void __launch_bounds__(kPartThreads, PW == 1 ? 2 : 1) k_part_build(Pa
     mbar_init(&bar, 1);
     ctl.abort = 0;
     ctl.next_gp = atomicAdd(p.ticket, 1u);
-    ctl.next_issued = issue_stage<PW>(p, ctl.next_gp, raw_key, raw_pay, &bar);
+    ctl.next_issued = issue_stage<PW>(p, ctl.next_gp, raw_key, raw_pay, &bar, &ctl.next_e0, &ctl.next_e1);
   }
   __syncthreads();
+  uint32_t last_j = 0xFFFFFFFFu;  // thread 32: the map held in sM[(iter & 1) ^ 1]
   for (;;) {
     const uint32_t gp = ctl.next_gp;
     const uint32_t issued = ctl.next_issued;
     if (gp >= p.P || ctl.abort) break;
     const uint32_t j = p.m == 1 ? 0u : upper_seg(p.part_seg, p.m, gp);
-    if (t == 32) sM[iter & 1] = load_map(p, j);  // visible after the barrier below
+    if (t == 32) {  // visible after the barrier below; global reads only when the map changes
+      sM[iter & 1] = j == last_j ? sM[(iter & 1) ^ 1] : load_map(p, j);
+      last_j = j;
+    }
     const MapRegs& M = sM[iter & 1];
     ++iter;
-    const uint64_t e0 = p.part_start[gp], e1 = p.part_start[gp + 1];
+    const uint64_t e0 = ctl.next_e0, e1 = ctl.next_e1;
     const uint32_t ne = uint32_t(e1 - e0 < 0xFFFFFFFFull ? e1 - e0 : 0xFFFFFFFFull);
     for (uint32_t i = t; i < (1u << p.logB); i += kPartThreads) cnt[i] = 0;
     if (issued) {  // bounded wait for the staged copy
@@ -1017,7 +1030,7 @@ __global__ void __launch_bounds__(kPartThreads, PW == 1 ? 2 : 1) k_part_build(Pa
     // the low warps first)
     if (t == kPartThreads - 32) {
       ctl.next_gp = atomicAdd(p.ticket, 1u);
-      ctl.next_issued = issue_stage<PW>(p, ctl.next_gp, raw_key, raw_pay, &bar);
+      ctl.next_issued = issue_stage<PW>(p, ctl.next_gp, raw_key, raw_pay, &bar, &ctl.next_e0, &ctl.next_e1);
     }
     if (early && ctl.skip) {
       __syncthreads();
@@ -1033,12 +1046,9 @@ __global__ void __launch_bounds__(kPartThreads, PW == 1 ? 2 : 1) k_part_build(Pa
       __syncthreads();
       continue;
     }
+    // the slot prefix is needed only by the write-out: resolved during the search
     search_partition<PW, true>(p, M, j, b0, nb, M.slot_base + ctl.excl, owner_mode, gkey, gpay, owner, gst,
-                               soff, att, work, ctl);
-    if (!early) {
-      if (t < 32) finish_prefix(p, M, gp, j, Sp, ctl);
-      __syncthreads();
-    }
+                               soff, att, work, ctl, !early, gp, Sp);
     if (!ctl.failed && !ctl.skip)
       write_partition<PW>(p, M, b0, nb, ctl.excl, owner_mode, gkey, gpay, owner, gst, soff, att, Sp);
     if (t == 0) flush_stats(p, j, ctl);
@@ -1101,7 +1111,7 @@ __global__ void __launch_bounds__(kPartThreads, 1) k_part_overflow(PassDev p) {
   }
   __syncthreads();
   search_partition<PW, false>(p, M, j, b0, nb, M.slot_base + excl, owner_mode, gkey, gpay, owner, gst, soff,
-                              att, work, ctl);
+                              att, work, ctl, false, gp, Sp);
   if (!ctl.failed)
     write_partition<PW>(p, M, b0, nb, excl, owner_mode, gkey, gpay, owner, gst, soff, att, Sp);
   if (t == 0) flush_stats(p, j, ctl);
