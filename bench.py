@@ -544,13 +544,10 @@ def main():
     h_found = torch.empty(nq, dtype=torch.uint8).pin_memory()
 
     def e2e_step():
-        keys.copy_(h_keys, non_blocking=True)
-        vals.copy_(h_vals, non_blocking=True)
-        queries.copy_(h_q, non_blocking=True)
-        m = F.fks_build_u64(keys, vals, SEED + rank)
-        F.fks_lookup_u64(m, queries, out, found, -1)
-        h_out.copy_(out, non_blocking=True)
-        h_found.copy_(found, non_blocking=True)
+        # the host-buffer entry points: upload + build, then needles streamed
+        # through the device in chunks (upload, lookup and download overlap)
+        m = F.fks_build_u64_host(h_keys, h_vals, SEED + rank)
+        F.fks_lookup_u64_host(m, h_q, h_out, h_found, -1)
         del m
 
     for _ in range(3):

@@ -354,6 +354,31 @@ fks_status fks_server_stats(fks_server_t srv, fks_server_stats_t* h_out);
 fks_map_t fks_server_map(fks_server_t srv, uint32_t map_id);
 void fks_server_destroy(fks_server_t srv);
 
+/* ------------------------------------------------------------------ host buffers
+ * The end-to-end path of a caller whose data lives in host memory; not in
+ * the paper (whose arrays live on the device).  Pinned buffers give
+ * asynchronous copies that overlap; pageable buffers work at the speed of
+ * the driver's staged copies.
+ *
+ * fks_build_u64_host -- fks_build_u64 over host keys and values: they are
+ * uploaded to device memory (stream-ordered pool), the map is built from the
+ * copies, which are freed afterwards.  Arguments as for fks_build_u64.
+ *
+ * fks_lookup_u64_host -- fks_lookup_u64 over host needles and results:
+ *   h_q       uint64[nq] needles (host)
+ *   h_out     int32[nq] / int64[nq] per the map's val_type (host), or NULL
+ *   h_found   uint8[nq] (host), or NULL
+ * The needles go through the device in chunks of 2^23: the upload of one
+ * chunk, the lookup of the previous one (on `stream`) and the download of
+ * the results before it overlap (three device buffers of the stream-ordered
+ * pool, two streams of the calling thread's own).  Blocks until the results
+ * are in host memory.  uint64 maps only (FKS_ERR_INVALID_ARG otherwise). */
+fks_status fks_build_u64_host(const uint64_t* h_keys, const void* h_vals, fks_val_type val_type, uint64_t n,
+                              uint64_t seed, const fks_build_opts* opts, const fks_allocator* alloc,
+                              fks_stream_t stream, fks_map_t* out);
+fks_status fks_lookup_u64_host(fks_map_t map, const uint64_t* h_q, uint64_t nq, void* h_out, uint8_t* h_found,
+                               int64_t absent, fks_stream_t stream);
+
 /* ------------------------------------------------------------------ tables
  * fks_map_info -- sizes and build statistics (host struct). */
 fks_status fks_map_info(fks_map_t map, fks_map_info_t* h_out);

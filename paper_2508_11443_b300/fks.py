@@ -94,6 +94,10 @@ def lib():
         L.fks_last_error.restype = ctypes.c_char_p
         L.fks_sortmap_build.argtypes = [vp, vp, ctypes.c_int, u64, vp, vp, ctypes.POINTER(vp)]
         L.fks_sortmap_build.restype = st
+        L.fks_build_u64_host.argtypes = [vp, vp, ctypes.c_int, u64, u64, vp, vp, vp, ctypes.POINTER(vp)]
+        L.fks_build_u64_host.restype = st
+        L.fks_lookup_u64_host.argtypes = [vp, vp, u64, vp, vp, i64, vp]
+        L.fks_lookup_u64_host.restype = st
         L.fks_eytzmap_build.argtypes = [vp, vp, ctypes.c_int, u64, vp, vp, ctypes.POINTER(vp)]
         L.fks_eytzmap_build.restype = st
         L.fks_sortmap_lookup.argtypes = [vp, vp, u64, vp, vp, i64, vp]
@@ -206,6 +210,40 @@ def fks_build_bytes(ctx, offs, vals, seed: int, opts: fks_build_opts | None = No
 def fks_lookup_u64(m: Map, q, out_vals=None, out_found=None, absent: int = -1, stream=None):
     _check(lib().fks_lookup_u64(m.handle, _ptr(q), q.numel(), _ptr(out_vals), _ptr(out_found),
                                 absent, _stream(stream)))
+
+
+def _hptr(a):
+    """Host address of a CPU tensor or numpy array (None passes NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return ctypes.c_void_p(a.ctypes.data)
+    assert not a.is_cuda, "host buffer expected"
+    return ctypes.c_void_p(a.data_ptr())
+
+
+def _hval_type(v) -> int:
+    dt = v.dtype
+    if dt in (np.int64, np.dtype(np.int64)) or str(dt) == "torch.int64":
+        return FKS_VAL_I64
+    if dt in (np.int32, np.dtype(np.int32)) or str(dt) == "torch.int32":
+        return FKS_VAL_I32
+    raise TypeError(f"values must be int32 or int64, got {dt}")
+
+
+def fks_build_u64_host(keys, vals, seed: int, opts: fks_build_opts | None = None, stream=None) -> Map:
+    """fks_build_u64 over host keys / values (numpy arrays or CPU tensors)."""
+    h = ctypes.c_void_p()
+    n = len(keys)
+    _check(lib().fks_build_u64_host(_hptr(keys), _hptr(vals), _hval_type(vals), n, seed & (2**64 - 1),
+                                    ctypes.byref(opts) if opts else None, None, _stream(stream), ctypes.byref(h)))
+    return Map(h.value)
+
+
+def fks_lookup_u64_host(m: Map, q, out_vals=None, out_found=None, absent: int = -1, stream=None):
+    """fks_lookup_u64 over host needles and results; blocks until done."""
+    _check(lib().fks_lookup_u64_host(m.handle, _hptr(q), len(q), _hptr(out_vals), _hptr(out_found), absent,
+                                     _stream(stream)))
 
 
 def fks_lookup_bytes(m: Map, qctx, qoffs, out_vals=None, out_found=None, absent: int = -1,
