@@ -163,6 +163,22 @@ fks_status fks_build_bytes(const uint8_t* ctx, const int64_t* offs, const void* 
                            const fks_build_opts* opts, const fks_allocator* alloc,
                            fks_stream_t stream, fks_map_t* out);
 
+/* fks_build_u64_async / fks_build_bytes_async -- the same builds, returned
+ * at once: the build runs on a host thread of the library (on `stream`, on
+ * the calling thread's current device) and the handle reports its outcome.
+ * fks_map_info waits for the build and returns its status (FKS_OK, or the
+ * error the blocking call would have returned); lookups, export and destroy
+ * wait for it as well.  A handle whose build failed holds no tables (every
+ * call on it returns the build's error) and must still be destroyed.  The
+ * inputs must stay valid until the build is known to be done. */
+fks_status fks_build_u64_async(const uint64_t* keys, const void* vals, fks_val_type val_type, uint64_t n,
+                               uint64_t seed, const fks_build_opts* opts, const fks_allocator* alloc,
+                               fks_stream_t stream, fks_map_t* out);
+fks_status fks_build_bytes_async(const uint8_t* ctx, const int64_t* offs, const void* vals,
+                                 fks_val_type val_type, uint64_t n, uint64_t seed,
+                                 const fks_build_opts* opts, const fks_allocator* alloc,
+                                 fks_stream_t stream, fks_map_t* out);
+
 /* ------------------------------------------------------------------ lookup
  * fks_lookup_u64 -- lookup -> opt v (Sec. 3.2) with the membership test of
  * Sec. 2.2: level-one descriptor, then one level-two slot, then a compare.
@@ -188,7 +204,8 @@ fks_status fks_lookup_bytes(fks_map_t map, const uint8_t* qctx, const int64_t* q
  * equal those of a per-call build of segment j with seed h_seeds[j].
  *   keys      uint64[total] for FKS_KEY_U64 (else NULL)
  *   ctx,offs  for FKS_KEY_BYTES: one context, offs int64[total+1] (else NULL)
- *   h_seg     int64[m+1] HOST segment offsets, h_seg[0] = 0, every segment
+ *   h_seg     int64[m+1] segment offsets in host or device memory (device
+ *             offsets are copied to the host first), h_seg[0] = 0, every segment
  *             non-empty
  *   h_seeds   uint64[m] HOST build seeds
  *   vals      int32/int64[total] (device)

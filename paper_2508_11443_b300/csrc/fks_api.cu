@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "fks.h"
@@ -169,6 +170,22 @@ struct Pinned {
 static thread_local Pinned g_pin_up, g_pin_down;
 
 // ---------------------------------------------------------------- handles
+// A build started by fks_build_*_async: the host thread running it, and
+// what it reports.  Every use of the handle joins the thread first.
+struct AsyncBuild {
+  std::mutex mu;
+  std::thread worker;
+  bool joined = false;
+  fks_status status = FKS_OK;
+  std::string msg;
+  int64_t seg[2] = {0, 0};  // the call's own copies of its small host arguments
+  uint64_t seed = 0;
+  fks_build_opts opts{};
+  bool has_opts = false;
+  fks_allocator alloc{};
+  bool has_alloc = false;
+};
+
 struct fks_map {
   fks_key_kind kind = FKS_KEY_U64;
   fks_val_type vt = FKS_VAL_I64;
@@ -186,7 +203,22 @@ struct fks_map {
   void* block = nullptr;
   size_t block_bytes = 0;
   Alloc alloc{nullptr};
+  AsyncBuild* async = nullptr;  // set for handles of fks_build_*_async
 };
+
+// Wait for the build of an asynchronous handle; its status (FKS_OK for
+// synchronous handles).  A failed build leaves an empty handle.
+static fks_status settle(fks_map* m) {
+  if (!m || !m->async) return FKS_OK;
+  AsyncBuild* a = m->async;
+  std::lock_guard<std::mutex> lock(a->mu);
+  if (!a->joined) {
+    a->worker.join();
+    a->joined = true;
+  }
+  if (a->status != FKS_OK) g_last_error = a->msg;
+  return a->status;
+}
 
 struct fks_mapset {
   fks_key_kind kind = FKS_KEY_U64;
@@ -753,7 +785,7 @@ static fks_status build_single(const BuildIn& in, const fks_build_opts* opts,
 // Lookup view of a map handle, for the serving loop (fks_serve.cu).
 namespace fks {
 bool lookup_view_of(fks_map_t m, LookupMap* out, int* strings, int* out_i64) {
-  if (!m || !m->desc) return false;
+  if (!m || settle(m) != FKS_OK || !m->desc) return false;
   *out = lookup_view(*m);
   *strings = m->kind == FKS_KEY_BYTES;
   *out_i64 = m->vt == FKS_VAL_I64;
@@ -792,13 +824,89 @@ fks_status fks_build_bytes(const uint8_t* ctx, const int64_t* offs, const void* 
   return build_single(in, opts, alloc, reinterpret_cast<cudaStream_t>(stream), out);
 }
 
+// Start a build on a host thread of its own; the handle is returned at once.
+static fks_status build_async(BuildIn in, const fks_build_opts* opts, const fks_allocator* alloc,
+                              fks_stream_t stream, fks_map_t* out) {
+  fks_map* shell = new fks_map();
+  shell->kind = in.kind;
+  shell->vt = in.vt;
+  AsyncBuild* a = new AsyncBuild();
+  shell->async = a;
+  a->seg[1] = in.seg[1];
+  a->seed = in.seeds[0];
+  if (opts) {
+    const size_t nb = opts->struct_size < sizeof(fks_build_opts) ? opts->struct_size : sizeof(fks_build_opts);
+    memcpy(&a->opts, opts, nb);
+    a->has_opts = true;
+  }
+  if (alloc) {
+    a->alloc = *alloc;
+    a->has_alloc = true;
+  }
+  in.seg = a->seg;
+  in.seeds = &a->seed;
+  int device = 0;
+  cudaGetDevice(&device);  // the current device is per host thread
+  try {
+    a->worker = std::thread([shell, a, in, stream, device]() {
+      cudaSetDevice(device);
+      fks_map_t built = nullptr;
+      const fks_status st = build_single(in, a->has_opts ? &a->opts : nullptr, a->has_alloc ? &a->alloc : nullptr,
+                                         reinterpret_cast<cudaStream_t>(stream), &built);
+      a->status = st;
+      if (st != FKS_OK) {
+        a->msg = g_last_error;  // this worker thread's message
+        return;
+      }
+      *shell = *built;  // the built tables now belong to the shell
+      shell->async = a;
+      delete built;
+    });
+  } catch (...) {
+    delete a;
+    delete shell;
+    return fail(FKS_ERR_OUT_OF_MEMORY, "could not start the build thread");
+  }
+  *out = shell;
+  return FKS_OK;
+}
+
+fks_status fks_build_u64_async(const uint64_t* keys, const void* vals, fks_val_type val_type, uint64_t n,
+                               uint64_t seed, const fks_build_opts* opts, const fks_allocator* alloc,
+                               fks_stream_t stream, fks_map_t* out) {
+  if (!out) return fail(FKS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!keys || !vals || n == 0 || n >= (1ull << 30) ||
+      (val_type != FKS_VAL_I32 && val_type != FKS_VAL_I64))
+    return fail(FKS_ERR_INVALID_ARG, "fks_build_u64_async: bad keys, vals, n or val_type");
+  const int64_t seg[2] = {0, int64_t(n)};
+  BuildIn in{FKS_KEY_U64, keys, nullptr, nullptr, vals, val_type, 1, seg, &seed};
+  return build_async(in, opts, alloc, stream, out);
+}
+
+fks_status fks_build_bytes_async(const uint8_t* ctx, const int64_t* offs, const void* vals,
+                                 fks_val_type val_type, uint64_t n, uint64_t seed,
+                                 const fks_build_opts* opts, const fks_allocator* alloc,
+                                 fks_stream_t stream, fks_map_t* out) {
+  if (!out) return fail(FKS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!ctx || !offs || !vals || n == 0 || n >= (1ull << 30) ||
+      (val_type != FKS_VAL_I32 && val_type != FKS_VAL_I64))
+    return fail(FKS_ERR_INVALID_ARG, "fks_build_bytes_async: bad ctx, offs, vals, n or val_type");
+  const int64_t seg[2] = {0, int64_t(n)};
+  BuildIn in{FKS_KEY_BYTES, nullptr, ctx, offs, vals, val_type, 1, seg, &seed};
+  return build_async(in, opts, alloc, stream, out);
+}
+
 static bool absent_fits(const fks_map* m, int64_t absent) {
   return m->vt == FKS_VAL_I64 || (absent >= INT32_MIN && absent <= INT32_MAX);
 }
 
 fks_status fks_lookup_u64(fks_map_t map, const uint64_t* q, uint64_t nq, void* out_vals,
                           uint8_t* out_found, int64_t absent, fks_stream_t stream) {
-  if (!map || map->kind != FKS_KEY_U64) return fail(FKS_ERR_INVALID_ARG, "fks_lookup_u64: not a u64 map");
+  if (!map) return fail(FKS_ERR_INVALID_ARG, "fks_lookup_u64: NULL map");
+  if (const fks_status bs = settle(map)) return bs;
+  if (map->kind != FKS_KEY_U64) return fail(FKS_ERR_INVALID_ARG, "fks_lookup_u64: not a u64 map");
   if (nq == 0) return FKS_OK;
   if (!q || !absent_fits(map, absent)) return fail(FKS_ERR_INVALID_ARG, "fks_lookup_u64: bad arguments");
   FKS_CUDA(launch_lookup_u64(lookup_view(*map), q, nq, out_vals, map->vt == FKS_VAL_I64, out_found,
@@ -809,7 +917,9 @@ fks_status fks_lookup_u64(fks_map_t map, const uint64_t* q, uint64_t nq, void* o
 fks_status fks_lookup_bytes(fks_map_t map, const uint8_t* qctx, const int64_t* qoffs, uint64_t nq,
                             void* out_vals, uint8_t* out_found, int64_t absent,
                             fks_stream_t stream) {
-  if (!map || map->kind != FKS_KEY_BYTES) return fail(FKS_ERR_INVALID_ARG, "fks_lookup_bytes: not a string map");
+  if (!map) return fail(FKS_ERR_INVALID_ARG, "fks_lookup_bytes: NULL map");
+  if (const fks_status bs = settle(map)) return bs;
+  if (map->kind != FKS_KEY_BYTES) return fail(FKS_ERR_INVALID_ARG, "fks_lookup_bytes: not a string map");
   if (nq == 0) return FKS_OK;
   if (!qctx || !qoffs || !absent_fits(map, absent))
     return fail(FKS_ERR_INVALID_ARG, "fks_lookup_bytes: bad arguments");
@@ -827,6 +937,18 @@ fks_status fks_build_batched(fks_key_kind kind, const uint64_t* keys, const uint
   *out = nullptr;
   if (m == 0 || !h_seg || !h_seeds || !vals || (val_type != FKS_VAL_I32 && val_type != FKS_VAL_I64))
     return fail(FKS_ERR_INVALID_ARG, "fks_build_batched: bad arguments");
+  // segment offsets in device memory are brought to the host first
+  std::vector<int64_t> seg_copy;
+  {
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, h_seg) == cudaSuccess &&
+        (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged)) {
+      seg_copy.resize(size_t(m) + 1);
+      FKS_CUDA(cudaMemcpy(seg_copy.data(), h_seg, sizeof(int64_t) * (m + 1), cudaMemcpyDeviceToHost));
+      h_seg = seg_copy.data();
+    }
+    cudaGetLastError();
+  }
   if (kind == FKS_KEY_U64 ? !keys : (kind == FKS_KEY_BYTES ? (!ctx || !offs) : true))
     return fail(FKS_ERR_INVALID_ARG, "fks_build_batched: bad key arguments");
   if (h_seg[0] != 0) return fail(FKS_ERR_INVALID_ARG, "fks_build_batched: h_seg[0] != 0");
@@ -928,6 +1050,7 @@ fks_map_t fks_mapset_get(fks_mapset_t set, uint32_t j) {
 fks_status fks_map_info(fks_map_t map, fks_map_info_t* h_out) {
   if (!map || !h_out) return fail(FKS_ERR_INVALID_ARG, "fks_map_info: NULL argument");
   memset(h_out, 0, sizeof(*h_out));
+  if (const fks_status bs = settle(map)) return bs;
   h_out->n = map->n;
   h_out->seed = map->seed;
   h_out->slots = map->S;
@@ -950,6 +1073,7 @@ fks_status fks_map_info(fks_map_t map, fks_map_info_t* h_out) {
 fks_status fks_map_export(fks_map_t map, uint64_t* h_desc, void* h_slots, uint8_t* h_ctx,
                           fks_stream_t stream) {
   if (!map) return fail(FKS_ERR_INVALID_ARG, "fks_map_export: NULL map");
+  if (const fks_status bs = settle(map)) return bs;
   const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int W = map->kind == FKS_KEY_BYTES ? 4 : 2;
   if (h_desc) FKS_CUDA(cudaMemcpyAsync(h_desc, map->desc, sizeof(uint64_t) * map->nb, cudaMemcpyDeviceToHost, st));
@@ -962,7 +1086,16 @@ fks_status fks_map_export(fks_map_t map, uint64_t* h_desc, void* h_slots, uint8_
 }
 
 void fks_map_destroy(fks_map_t map) {
-  if (!map || !map->block) return;  // borrowed maps are freed with their set
+  if (!map) return;
+  if (map->async) {  // an asynchronous handle: join its build, then free what it built
+    settle(map);
+    delete map->async;
+    map->async = nullptr;
+    if (map->block) map->alloc.put(map->block, map->block_bytes, nullptr);
+    delete map;
+    return;
+  }
+  if (!map->block) return;  // borrowed maps are freed with their set
   map->alloc.put(map->block, map->block_bytes, nullptr);
   delete map;
 }

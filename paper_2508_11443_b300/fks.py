@@ -94,6 +94,10 @@ def lib():
         L.fks_last_error.restype = ctypes.c_char_p
         L.fks_sortmap_build.argtypes = [vp, vp, ctypes.c_int, u64, vp, vp, ctypes.POINTER(vp)]
         L.fks_sortmap_build.restype = st
+        L.fks_build_u64_async.argtypes = [vp, vp, ctypes.c_int, u64, u64, vp, vp, vp, ctypes.POINTER(vp)]
+        L.fks_build_u64_async.restype = st
+        L.fks_build_bytes_async.argtypes = [vp, vp, vp, ctypes.c_int, u64, u64, vp, vp, vp, ctypes.POINTER(vp)]
+        L.fks_build_bytes_async.restype = st
         L.fks_build_u64_host.argtypes = [vp, vp, ctypes.c_int, u64, u64, vp, vp, vp, ctypes.POINTER(vp)]
         L.fks_build_u64_host.restype = st
         L.fks_lookup_u64_host.argtypes = [vp, vp, u64, vp, vp, i64, vp]
@@ -197,6 +201,29 @@ def fks_build_u64(keys, vals, seed: int, opts: fks_build_opts | None = None, str
     return Map(h.value)
 
 
+def fks_build_u64_async(keys, vals, seed: int, opts: fks_build_opts | None = None, stream=None) -> Map:
+    """Start a build and return its handle at once; fks_map_info reports the outcome."""
+    h = ctypes.c_void_p()
+    _check(lib().fks_build_u64_async(_ptr(keys), _ptr(vals), _val_type(vals), keys.numel(), seed & (2**64 - 1),
+                                     ctypes.byref(opts) if opts else None, None, _stream(stream),
+                                     ctypes.byref(h)))
+    return Map(h.value)
+
+
+def fks_build_bytes_async(ctx, offs, vals, seed: int, opts: fks_build_opts | None = None, stream=None) -> Map:
+    h = ctypes.c_void_p()
+    _check(lib().fks_build_bytes_async(_ptr(ctx), _ptr(offs), _ptr(vals), _val_type(vals), offs.numel() - 1,
+                                       seed & (2**64 - 1), ctypes.byref(opts) if opts else None, None,
+                                       _stream(stream), ctypes.byref(h)))
+    return Map(h.value)
+
+
+def fks_map_status(m: Map) -> int:
+    """The status fks_map_info returns (waits for an asynchronous build)."""
+    info = fks_map_info_t()
+    return int(lib().fks_map_info(m.handle, ctypes.byref(info)))
+
+
 def fks_build_bytes(ctx, offs, vals, seed: int, opts: fks_build_opts | None = None,
                     stream=None) -> Map:
     h = ctypes.c_void_p()
@@ -254,13 +281,18 @@ def fks_lookup_bytes(m: Map, qctx, qoffs, out_vals=None, out_found=None, absent:
 
 def fks_build_batched(kind: int, keys, ctx, offs, seg: np.ndarray, seeds: np.ndarray, vals,
                       opts: fks_build_opts | None = None, stream=None, raise_on_error=True) -> MapSet:
-    seg = np.ascontiguousarray(seg, np.int64)
+    if getattr(seg, "is_cuda", False):  # device segment offsets: passed as they are
+        m = seg.numel() - 1
+        seg_ptr = _ptr(seg)
+    else:
+        seg = np.ascontiguousarray(seg, np.int64)
+        m = seg.size - 1
+        seg_ptr = seg.ctypes.data_as(ctypes.c_void_p)
     seeds = np.ascontiguousarray(seeds, np.uint64)
-    m = seg.size - 1
     status = np.zeros(m, np.int32)
     h = ctypes.c_void_p()
     st = lib().fks_build_batched(kind, _ptr(keys), _ptr(ctx), _ptr(offs),
-                                 seg.ctypes.data_as(ctypes.c_void_p),
+                                 seg_ptr,
                                  seeds.ctypes.data_as(ctypes.c_void_p), m, _ptr(vals),
                                  _val_type(vals), ctypes.byref(opts) if opts else None, None,
                                  _stream(stream), ctypes.byref(h), status.ctypes.data_as(ctypes.c_void_p))
