@@ -196,6 +196,28 @@ def dist_setup():
     return world, rank, local
 
 
+# Several GPUs run replicas (weak scaling): every rank builds and queries a
+# map of its own from its own key stream, with no collective in the data
+# path; the job's time is the slowest rank's and its throughput counts the
+# work of all ranks.
+def rank_seed(rank: int) -> int:
+    return SEED + rank
+
+
+def max_over_ranks(ms: float, world: int, device) -> float:
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: int, world: int, ms_per_step: float) -> float:
+    return units_per_rank * world / (ms_per_step / 1e3)
+
+
 def cpu_sample_run(n: int, nq: int, seed: int):
     """Oracle build + lookup over a sample of the workload; returns seconds."""
     import oracle as O
@@ -469,7 +491,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     n = args.n
     nq = n
-    w = W.u64_workload(n, nq, HIT, SEED + rank)
+    w = W.u64_workload(n, nq, HIT, rank_seed(rank))
     keys = torch.from_numpy(w.keys.view(np.int64)).cuda()
     vals = torch.from_numpy(w.vals).cuda()
     queries = torch.from_numpy(w.queries.view(np.int64)).cuda()
@@ -483,7 +505,7 @@ def main():
     def step(timed):
         e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         e0.record(stream)
-        m = F.fks_build_u64(keys, vals, SEED + rank)
+        m = F.fks_build_u64(keys, vals, rank_seed(rank))
         e1.record(stream)
         F.fks_lookup_u64(m, queries, out, found, -1)
         e2.record(stream)
@@ -527,14 +549,10 @@ def main():
         if world > 1:
             dist.barrier()
     launches = F.fks_kernel_launches() - launches0
-    total_ms = t_start.elapsed_time(t_end)
-    if world > 1:
-        tt = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(t_start.elapsed_time(t_end), world, "cuda")
     ms_per_step = total_ms / args.steps
     units = (n + nq) * world
-    value = units / (ms_per_step / 1e3)
+    value = job_throughput(n + nq, world, ms_per_step)
 
     # ---- end to end through the C ABI from pinned host memory
     h_keys = torch.from_numpy(w.keys.view(np.int64)).pin_memory()
@@ -546,7 +564,7 @@ def main():
     def e2e_step():
         # the host-buffer entry points: upload + build, then needles streamed
         # through the device in chunks (upload, lookup and download overlap)
-        m = F.fks_build_u64_host(h_keys, h_vals, SEED + rank)
+        m = F.fks_build_u64_host(h_keys, h_vals, rank_seed(rank))
         F.fks_lookup_u64_host(m, h_q, h_out, h_found, -1)
         del m
 
@@ -562,11 +580,7 @@ def main():
         e2e_step()
     b.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = a.elapsed_time(b) / e2e_steps
-    if world > 1:
-        tt = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = max_over_ranks(a.elapsed_time(b) / e2e_steps, world, "cuda")
     assert np.array_equal(h_found.numpy(), w.expect_found)
 
     # ---- roofline of the dominant kernel
