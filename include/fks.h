@@ -230,6 +230,119 @@ fks_status fks_lookup_batched(fks_mapset_t set, const uint32_t* map_ids, const u
 uint32_t fks_mapset_size(fks_mapset_t set);
 fks_map_t fks_mapset_get(fks_mapset_t set, uint32_t j);
 
+/* ------------------------------------------------------------------ recorded batched builds
+ * A batched build recorded once as a CUDA graph and replayed: for a caller
+ * that rebuilds the same set of maps again and again from refreshed data
+ * (same buffers, same segment sizes), so that each rebuild costs one graph
+ * launch instead of a dozen kernel launches and table uploads.  The paper
+ * builds each map once; this is the launch-sequence form of its batched
+ * construction (one data-parallel pass over all maps' keys, Sec. 2.5).
+ *
+ * fks_build_graph_create -- arguments as for fks_build_batched, without the
+ * seeds: the input buffers (keys, or ctx/offs; vals) are bound to the graph
+ * and must stay valid until it is destroyed; their contents may change
+ * between runs, but not their sizes (for string keys offs[total], the
+ * context size, must stay the same).  Allocates the set's tables and the
+ * build's scratch once, and records the first pass (every map at level-one
+ * round 0: table upload, fingerprints, grouping, partition build, status
+ * download) as a graph on a stream of the library's own.  dedup = 1 is
+ * rejected (it changes the sizes).  Synchronises `stream`.
+ *
+ * fks_build_graph_run -- rebuild every map from the buffers' current
+ * contents with seeds h_seeds[m] (host): one launch of the recorded pass on
+ * `stream`, one synchronisation, then the maps that must redraw (a space
+ * bound or level-two failure, probability well below 1/2 per map) run
+ * through the ordinary pass loop.  The tables equal those of
+ * fks_build_batched with the same inputs and seeds.  h_status[m] (nullable)
+ * receives each map's status; returns FKS_OK only if every map was built.
+ * Runs of one graph are serialised; a run blocks until it is done.
+ *
+ * fks_build_graph_mapset -- the maps of the last run, for fks_lookup_batched,
+ * fks_mapset_get, export and info.  Owned by the graph: valid until
+ * fks_build_graph_destroy (fks_mapset_destroy on it does nothing); each run
+ * rewrites its tables in place, so lookups must not overlap a run.
+ *
+ * fks_build_graph_kernels -- kernels one replay of the recorded pass runs. */
+typedef struct fks_build_graph* fks_build_graph_t;
+fks_status fks_build_graph_create(fks_key_kind kind, const uint64_t* keys, const uint8_t* ctx,
+                                  const int64_t* offs, const int64_t* h_seg, uint32_t m, const void* vals,
+                                  fks_val_type val_type, const fks_build_opts* opts, const fks_allocator* alloc,
+                                  fks_stream_t stream, fks_build_graph_t* out);
+fks_status fks_build_graph_run(fks_build_graph_t g, const uint64_t* h_seeds, fks_stream_t stream,
+                               fks_status* h_status);
+fks_mapset_t fks_build_graph_mapset(fks_build_graph_t g);
+uint32_t fks_build_graph_kernels(fks_build_graph_t g);
+void fks_build_graph_destroy(fks_build_graph_t g);
+
+/* ------------------------------------------------------------------ launch shapes and the autotuner
+ * How a build and a uint64 lookup spread their work over the GPU.  No shape
+ * changes a table or a result: every level-two search keeps the first
+ * attempt without a collision, whichever threads run it.  The paper leaves
+ * this mapping to its compiler; here it is measured.
+ *
+ *   thread_search_max      buckets of 2 .. T keys are searched by one thread
+ *                          each (a register bitmap of the s^2 slots); larger
+ *                          ones by a warp segment of 2^ceil(log2 s) lanes,
+ *                          above 32 keys by the whole CTA: the threads per
+ *                          bucket and the small / large bucket threshold (1..3)
+ *   part_ctas_per_sm       resident partition-build CTAs per SM (0 = as many
+ *                          as fit, else 1 or 2)
+ *   scatter_blocks_per_sm  blocks per SM of the one-level count / scatter (1..64)
+ *   split_min_keys_log2    passes of >= 2^x keys are grouped in two radix
+ *                          levels instead of one (10..40)
+ *   lookup_queries_per_thread, lookup_block, lookup_blocks_per_sm
+ *                          needles in flight per thread (2, 4, 8), threads
+ *                          per block (128, 256, 512) and the grid in blocks
+ *                          per SM (1..64) of fks_lookup_u64
+ * A process-wide table holds one entry per (key_kind, keys_per_bucket);
+ * builds and uint64 lookups of maps with that lambda use it, else the
+ * defaults (3 or 1, 0, 8, 20, 4, 256, 8). */
+typedef struct {
+  size_t struct_size;           /* sizeof(fks_tuning)                            */
+  uint32_t key_kind;            /* fks_key_kind of the entry                     */
+  uint32_t keys_per_bucket;     /* lambda of the entry                           */
+  uint32_t thread_search_max;
+  uint32_t part_ctas_per_sm;
+  uint32_t scatter_blocks_per_sm;
+  uint32_t split_min_keys_log2;
+  uint32_t lookup_queries_per_thread; /* lookup fields: FKS_KEY_U64 entries only */
+  uint32_t lookup_block;
+  uint32_t lookup_blocks_per_sm;
+  uint32_t tuned;               /* 1: measured by fks_autotune                   */
+  float build_ms;               /* the sample build at the chosen shape          */
+  float lookup_ms;              /* the sample lookup at the chosen shape         */
+  uint64_t sample_keys;         /* keys of the sample it was measured on         */
+} fks_tuning;
+
+/* One measured candidate: param 0 thread_search_max, 1 part_ctas_per_sm,
+ * 2 scatter_blocks_per_sm, 3 split_min_keys_log2, 4 lookup_queries_per_thread
+ * << 16 | lookup_block, 5 lookup_blocks_per_sm; ms is the median time. */
+typedef struct {
+  uint32_t param;
+  uint32_t value;
+  float ms;
+} fks_tune_trial;
+
+/* fks_autotune -- measure the shapes on a synthetic sample and keep the
+ * fastest in the table.  The sample: n keys (0: 2^22; 1024 <= n < 2^30) from
+ * a splitmix64 stream for FKS_KEY_U64, or distinct a-z strings of 8..64
+ * bytes for FKS_KEY_BYTES; uint64 lookups of nq needles (0: n) at about 90 %
+ * hits.  Coordinate descent from the current entry: each build candidate is
+ * the median of three blocking builds, each lookup candidate the median of
+ * five launches (CUDA events).  h_out (nullable) receives the entry,
+ * h_trials[max_trials] (nullable) the candidates measured and *h_count their
+ * number.  Allocates the sample with cudaMallocAsync on `stream`; blocks. */
+fks_status fks_autotune(fks_key_kind kind, uint32_t keys_per_bucket, uint64_t n, uint64_t nq, uint64_t seed,
+                        fks_stream_t stream, fks_tuning* h_out, fks_tune_trial* h_trials, uint32_t max_trials,
+                        uint32_t* h_count);
+/* the entry in effect for (kind, keys_per_bucket): tuned, or the defaults */
+fks_status fks_tuning_get(fks_key_kind kind, uint32_t keys_per_bucket, fks_tuning* h_out);
+/* install an entry (e.g. one saved from an earlier process); every field is
+ * checked against the ranges above (FKS_ERR_INVALID_ARG otherwise) */
+fks_status fks_tuning_set(const fks_tuning* h_in);
+/* forget every entry: back to the defaults */
+void fks_tuning_reset(void);
+
 /* ------------------------------------------------------------------ no allocation
  * fks_build_u64_noalloc -- the same build as fks_build_u64, for callers that
  * must not allocate device memory: a service whose device memory is all

@@ -228,6 +228,7 @@ struct fks_mapset {
   void* block = nullptr;
   size_t block_bytes = 0;
   Alloc alloc{nullptr};
+  bool borrowed = false;  // the set of a recorded build: freed with it
 };
 
 struct fks_sortmap {
@@ -284,11 +285,6 @@ static bool read_opts(const fks_build_opts* o, Opts* out) {
   return true;
 }
 
-// Buckets of up to this many keys are searched by a single thread, larger
-// ones by packed warp segments (measured on 2^26-key builds: 3 for small
-// buckets; with 8 or 16 keys per bucket every bucket goes to a segment).
-static uint32_t thread_search_max(uint32_t lambda) { return lambda <= 4 ? kThreadSearchMax : 1u; }
-
 // Slot offsets are 32-bit descriptor fields: bound * n must stay below 2^32.
 static bool sizes_fit(const Opts& o, uint64_t n) { return uint64_t(o.bound) * n <= 0xFFFFFFFFull; }
 
@@ -298,8 +294,6 @@ static thread_local int g_hold_first_partition = 0;
 extern "C" void fks_test_hold_first_partition(int on) { g_hold_first_partition = on; }
 
 // ---------------------------------------------------------------- the build
-// Passes with at least this many keys group them in two radix levels.
-constexpr uint64_t kSplitMinKeys = 1ull << 20;
 
 struct BuildIn {
   fks_key_kind kind;
@@ -321,18 +315,102 @@ struct SetMem {
   std::vector<uint64_t> desc_base;  // per map
 };
 
-static fks_status build_impl(const BuildIn& in, const Opts& o, const Alloc& A, cudaStream_t st,
-                             void** out_block, size_t* out_block_bytes, SetMem* mem,
-                             std::vector<fks_map>* maps_out, std::vector<fks_status>* per_map) {
-  const uint32_t m = in.m;
-  const bool str = in.kind == FKS_KEY_BYTES;
-  const int PW = str ? 2 : 1;
-  const int W = str ? 4 : 2;  // words per slot
-  const uint64_t total = uint64_t(in.seg[m]);
-  const uint32_t logB = part_log_buckets(o.lambda);
-  const uint64_t B = 1ull << logB;
+// A build of m maps over one input.  init allocates the set's tables and the
+// scratch of its passes once; enqueue_pass puts one pass of the device
+// pipeline on a stream -- pass-table upload, kernels, status download --
+// with no host synchronisation in it, so that a pass can be recorded as a
+// CUDA graph; run is the host loop over level-one rounds: after each pass
+// the per-map status words decide which maps are done and which redraw.
+struct GraphPass;
+
+struct SetBuild {
+  BuildIn in{};
+  Opts o{};
+  Alloc A{nullptr};
+  uint32_t m = 0;
+  bool str = false;
+  int PW = 1, W = 2;
+  uint64_t total = 0;
+  uint32_t logB = 0;
+  uint64_t B = 0;
+  std::vector<uint64_t> nbs;
+  uint64_t ctx_bytes = 0;
+  uint8_t* block = nullptr;  // the set's tables (desc, slots, context)
+  size_t block_bytes = 0;
+  uint8_t* scr = nullptr;    // scratch of the passes
+  size_t scr_bytes = 0;
+  SetMem mem;
+  PassDev p{};
+  MapDev* d_maps = nullptr;
+  uint64_t* d_pseg = nullptr;
+  uint32_t* d_qseg = nullptr;
+  MapStatus* d_stat = nullptr;
+  uint64_t* fps = nullptr;
+  BuildShape bs{};  // launch shape (fks_tune.cu)
+  SplitShape shape{};
+  bool use_split = false;
+  size_t hist_words = 0;
+  size_t s_ka = 0, s_pa = 0, s_ga = 0, s_hist = 0, s_sums = 0, s_sa = 0, s_tb = 0;
+  uint64_t* ovf_key = nullptr;
+  size_t ovf_bytes = 0;
+  int sms = 0;
+  uint32_t levels = 1;  // grouping levels of the last pass
+  // outcome of the last run
+  std::vector<uint32_t> round;
+  std::vector<fks_status> per_map;
+  std::vector<fks_map> maps;
+  fks_build_profile profile{};
+
+  // pinned pass tables: MapDev[ma] | pass offsets u64[ma+1] | partition offsets u32[ma+1]
+  static size_t up_bytes(uint32_t ma) {
+    return sizeof(MapDev) * ma + sizeof(uint64_t) * (ma + 1) + sizeof(uint32_t) * (ma + 1);
+  }
+  // pinned status: MapStatus[ma] | overflow count
+  static size_t down_bytes(uint32_t ma) { return sizeof(MapStatus) * ma + 16; }
+
+  fks_status init(const BuildIn& in_, const Opts& o_, const Alloc& A_, cudaStream_t st);
+  uint32_t fill_tables(const std::vector<uint32_t>& active, uint8_t* up);
+  cudaError_t enqueue_pass(uint32_t ma, const uint8_t* up, uint8_t* down, bool copy_ctx, ProfileEvents* prof,
+                           cudaStream_t st);
+  fks_status run(cudaStream_t st, GraphPass* g);
+  void free_scratch(cudaStream_t st) {
+    if (ovf_key) A.put(ovf_key, ovf_bytes, st);
+    ovf_key = nullptr;
+    if (scr) A.put(scr, scr_bytes, st);
+    scr = nullptr;
+  }
+  void free_tables(cudaStream_t st) {
+    if (block) A.put(block, block_bytes, st);
+    block = nullptr;
+  }
+};
+
+// A pass recorded as a CUDA graph: its tables are read from, and its status
+// written to, pinned buffers owned here, so that a launch of the graph
+// builds from whatever the host put there.
+struct GraphPass {
+  cudaGraphExec_t exec = nullptr;
+  uint8_t* up = nullptr;
+  uint8_t* down = nullptr;
+  uint32_t kernels = 0;  // kernel nodes of the graph
+};
+
+fks_status SetBuild::init(const BuildIn& in_, const Opts& o_, const Alloc& A_, cudaStream_t st) {
+  in = in_;
+  o = o_;
+  A = A_;
+  m = in.m;
+  str = in.kind == FKS_KEY_BYTES;
+  PW = str ? 2 : 1;
+  W = str ? 4 : 2;  // words per slot
+  total = uint64_t(in.seg[m]);
+  logB = part_log_buckets(o.lambda);
+  B = 1ull << logB;
+  sms = sm_count();
+  bs = build_shape_for(int(in.kind), o.lambda);
   uint64_t slot_total = 0, desc_total = 0;
-  std::vector<uint64_t> slot_base(m), desc_base(m), nbs(m);
+  std::vector<uint64_t> slot_base(m), desc_base(m);
+  nbs.assign(m, 0);
   for (uint32_t j = 0; j < m; ++j) {
     const uint64_t n = uint64_t(in.seg[j + 1] - in.seg[j]);
     if (!sizes_fit(o, n)) return fail(FKS_ERR_INVALID_ARG, "bound_factor * n does not fit 32-bit slot offsets");
@@ -343,7 +421,6 @@ static fks_status build_impl(const BuildIn& in, const Opts& o, const Alloc& A, c
     desc_total += nbs[j];
   }
   // context bytes: offs[total] from the device
-  uint64_t ctx_bytes = 0;
   if (str) {
     int64_t last = 0;
     FKS_CUDA(cudaMemcpyAsync(&last, in.offs + total, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -356,20 +433,14 @@ static fks_status build_impl(const BuildIn& in, const Opts& o, const Alloc& A, c
   const size_t o_desc = cm.take<uint64_t>(desc_total);
   const size_t o_slots = cm.take<uint64_t>(slot_total * W);
   const size_t o_ctx = cm.take<uint8_t>(str ? ctx_bytes + 16 : 0);
-  uint8_t* block = static_cast<uint8_t*>(A.get(cm.off, st));
+  block = static_cast<uint8_t*>(A.get(cm.off, st));
   if (!block) return fail(FKS_ERR_OUT_OF_MEMORY, "allocation of map tables failed");
-  mem->desc = reinterpret_cast<uint64_t*>(block + o_desc);
-  mem->slots = reinterpret_cast<uint64_t*>(block + o_slots);
-  mem->ctx = str ? block + o_ctx : nullptr;
-  mem->slot_base = slot_base;
-  mem->desc_base = desc_base;
-  if (str && ctx_bytes) {
-    cudaError_t e = cudaMemcpyAsync(mem->ctx, in.ctx, ctx_bytes, cudaMemcpyDeviceToDevice, st);
-    if (e != cudaSuccess) {
-      A.put(block, cm.off, st);
-      return cuda_fail(e, "context copy");
-    }
-  }
+  block_bytes = cm.off;
+  mem.desc = reinterpret_cast<uint64_t*>(block + o_desc);
+  mem.slots = reinterpret_cast<uint64_t*>(block + o_slots);
+  mem.ctx = str ? block + o_ctx : nullptr;
+  mem.slot_base = slot_base;
+  mem.desc_base = desc_base;
   // scratch for the largest pass (the first one holds every map)
   uint64_t P_all = 0;
   for (uint32_t j = 0; j < m; ++j) P_all += (nbs[j] + B - 1) / B;
@@ -389,10 +460,8 @@ static fks_status build_impl(const BuildIn& in, const Opts& o, const Alloc& A, c
   const size_t s_stat = cs.take<MapStatus>(m);
   const size_t s_fps = cs.take<uint64_t>(str ? total + 1 : 0);
   // two-level grouping for large builds
-  const SplitShape shape = split_shape(uint32_t(P_all), total);
-  const bool use_split = total >= kSplitMinKeys && shape.ok;
-  size_t s_ka = 0, s_pa = 0, s_ga = 0, s_hist = 0, s_sums = 0, s_sa = 0, s_tb = 0;
-  size_t hist_words = 0;
+  shape = split_shape(uint32_t(P_all), total);
+  use_split = total >= (1ull << bs.split_min_log2) && shape.ok;
   if (use_split) {
     hist_words = split_hist_words(shape);
     s_ka = cs.take<uint64_t>(total);
@@ -403,15 +472,13 @@ static fks_status build_impl(const BuildIn& in, const Opts& o, const Alloc& A, c
     s_sa = cs.take<uint64_t>(shape.binsA + 1);
     s_tb = cs.take<uint32_t>(shape.binsA + 1);
   }
-  uint8_t* scr = static_cast<uint8_t*>(A.get(cs.off, st));
+  scr = static_cast<uint8_t*>(A.get(cs.off, st));
   if (!scr) {
-    A.put(block, cm.off, st);
+    free_tables(st);
     return fail(FKS_ERR_OUT_OF_MEMORY, "allocation of build scratch failed");
   }
-  uint64_t* ovf_key = nullptr;
-  size_t ovf_bytes = 0;
-
-  PassDev p{};
+  scr_bytes = cs.off;
+  p = PassDev{};
   p.part_cnt = reinterpret_cast<uint32_t*>(scr + s_cnt);
   p.part_start = reinterpret_cast<uint32_t*>(scr + s_start);
   p.part_cursor = reinterpret_cast<uint32_t*>(scr + s_cursor);
@@ -422,11 +489,11 @@ static fks_status build_impl(const BuildIn& in, const Opts& o, const Alloc& A, c
   p.ovf_excl = reinterpret_cast<uint64_t*>(scr + s_ove);
   p.stage_key = reinterpret_cast<uint64_t*>(scr + s_skey);
   p.stage_pay = reinterpret_cast<uint64_t*>(scr + s_spay);
-  MapDev* d_maps = reinterpret_cast<MapDev*>(scr + s_maps);
-  uint64_t* d_pseg = reinterpret_cast<uint64_t*>(scr + s_pseg);
-  uint32_t* d_qseg = reinterpret_cast<uint32_t*>(scr + s_qseg);
-  MapStatus* d_stat = reinterpret_cast<MapStatus*>(scr + s_stat);
-  uint64_t* fps = str ? reinterpret_cast<uint64_t*>(scr + s_fps) : nullptr;
+  d_maps = reinterpret_cast<MapDev*>(scr + s_maps);
+  d_pseg = reinterpret_cast<uint64_t*>(scr + s_pseg);
+  d_qseg = reinterpret_cast<uint32_t*>(scr + s_qseg);
+  d_stat = reinterpret_cast<MapStatus*>(scr + s_stat);
+  fps = str ? reinterpret_cast<uint64_t*>(scr + s_fps) : nullptr;
   p.maps = d_maps;
   p.status = d_stat;
   p.pass_seg = d_pseg;
@@ -435,147 +502,183 @@ static fks_status build_impl(const BuildIn& in, const Opts& o, const Alloc& A, c
   p.vals = in.vals;
   p.vals_i64 = in.vt == FKS_VAL_I64;
   p.offs = in.offs;
-  p.ctx = mem->ctx;
-  p.desc = mem->desc;
-  p.slots = mem->slots;
+  p.ctx = mem.ctx;
+  p.desc = mem.desc;
+  p.slots = mem.slots;
   p.logB = logB;
   p.cfg.attempt_cap = o.attempt_cap;
   p.cfg.reject = o.reject;
   p.cfg.spin_limit = o.spin;
   p.cfg.hold_first = uint32_t(g_hold_first_partition);
-  p.cfg.thread_max = thread_search_max(o.lambda);
+  p.cfg.thread_max = bs.thread_max;
+  return FKS_OK;
+}
 
-  std::vector<uint32_t> round(m, 0);
+// Pass tables of the `active` maps at their current rounds into `up`; sets
+// the pass geometry (p.m, p.P, p.total).
+uint32_t SetBuild::fill_tables(const std::vector<uint32_t>& active, uint8_t* up) {
+  const uint32_t ma = uint32_t(active.size());
+  MapDev* h_maps = reinterpret_cast<MapDev*>(up);
+  uint64_t* h_pseg = reinterpret_cast<uint64_t*>(up + sizeof(MapDev) * ma);
+  uint32_t* h_qseg = reinterpret_cast<uint32_t*>(up + sizeof(MapDev) * ma + sizeof(uint64_t) * (ma + 1));
+  uint64_t pe = 0;
+  uint32_t pp = 0;
+  for (uint32_t a = 0; a < ma; ++a) {
+    const uint32_t j = active[a];
+    const uint64_t n = uint64_t(in.seg[j + 1] - in.seg[j]);
+    MapDev& M = h_maps[a];
+    M.key_begin = uint64_t(in.seg[j]);
+    M.pass_begin = pe;
+    M.desc_base = mem.desc_base[j];
+    M.slot_base = mem.slot_base[j];
+    M.seed = in.seeds[j];
+    M.round = round[j];
+    M.c1 = derive(M.seed, M.round, kTagLevel1, 0);
+    M.fpb = fp_base(M.seed, M.round);
+    M.n = uint32_t(n);
+    M.nb = uint32_t(nbs[j]);
+    M.slot_cap = uint32_t(uint64_t(o.bound) * n);
+    M.part_begin = pp;
+    h_pseg[a] = pe;
+    h_qseg[a] = pp;
+    pe += n;
+    pp += uint32_t((nbs[j] + B - 1) / B);
+  }
+  h_pseg[ma] = pe;
+  h_qseg[ma] = pp;
+  p.m = ma;
+  p.P = pp;
+  p.total = pe;
+  return ma;
+}
+
+cudaError_t SetBuild::enqueue_pass(uint32_t ma, const uint8_t* up, uint8_t* down, bool copy_ctx,
+                                   ProfileEvents* prof, cudaStream_t st) {
+  cudaError_t e;
+#define FKS_STEP(call) \
+  if ((e = (call)) != cudaSuccess) return e;
+  if (copy_ctx && str && ctx_bytes)
+    FKS_STEP(cudaMemcpyAsync(mem.ctx, in.ctx, ctx_bytes, cudaMemcpyDeviceToDevice, st));
+  FKS_STEP(cudaMemcpyAsync(d_maps, up, sizeof(MapDev) * ma, cudaMemcpyHostToDevice, st));
+  FKS_STEP(cudaMemcpyAsync(d_pseg, up + sizeof(MapDev) * ma, sizeof(uint64_t) * (ma + 1), cudaMemcpyHostToDevice, st));
+  FKS_STEP(cudaMemcpyAsync(d_qseg, up + sizeof(MapDev) * ma + sizeof(uint64_t) * (ma + 1),
+                           sizeof(uint32_t) * (ma + 1), cudaMemcpyHostToDevice, st));
+  FKS_STEP(cudaMemsetAsync(d_stat, 0, sizeof(MapStatus) * ma, st));
+  if (prof && str) cudaEventRecord(prof->fp0, st);
+  if (str) FKS_STEP(launch_fingerprints(in.ctx, in.offs, total, d_maps, d_pseg, ma, p.total, fps, d_stat, st));
+  if (prof && str) cudaEventRecord(prof->fp1, st);
+  const SplitShape sh = split_shape(p.P, p.total);
+  const bool split_pass = use_split && sh.ok && split_hist_words(sh) <= hist_words && sh.binsA <= shape.binsA &&
+                          p.total >= (1ull << bs.split_min_log2);
+  if (split_pass) {
+    SplitDev sd{};
+    sd.binsA = sh.binsA;
+    sd.binsB = sh.binsB;
+    sd.shiftB = sh.shiftB;
+    sd.tilesA = sh.tilesA;
+    sd.tilesB_max = sh.tilesB_max;
+    sd.histA = sd.histB = reinterpret_cast<uint32_t*>(scr + s_hist);
+    sd.sums = reinterpret_cast<uint32_t*>(scr + s_sums);
+    sd.startA = reinterpret_cast<uint64_t*>(scr + s_sa);
+    sd.tstartB = reinterpret_cast<uint32_t*>(scr + s_tb);
+    sd.keyA = reinterpret_cast<uint64_t*>(scr + s_ka);
+    sd.payA = reinterpret_cast<uint64_t*>(scr + s_pa);
+    sd.gpA = reinterpret_cast<uint32_t*>(scr + s_ga);
+    levels = 2;
+    FKS_STEP(launch_pass_split(p, sd, str, sms, bs, st, prof ? &prof->pe : nullptr));
+  } else {
+    levels = 1;
+    FKS_STEP(launch_pass(p, str, sms, bs, st, prof ? &prof->pe : nullptr));
+  }
+  MapStatus* h_stat = reinterpret_cast<MapStatus*>(down);
+  uint32_t* h_ovf = reinterpret_cast<uint32_t*>(down + sizeof(MapStatus) * ma);
+  FKS_STEP(cudaMemcpyAsync(h_stat, d_stat, sizeof(MapStatus) * ma, cudaMemcpyDeviceToHost, st));
+  FKS_STEP(cudaMemcpyAsync(h_ovf, p.ovf_count, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+#undef FKS_STEP
+  return cudaSuccess;
+}
+
+fks_status SetBuild::run(cudaStream_t st, GraphPass* g) {
+  round.assign(m, 0);
   std::vector<uint32_t> active(m);
   for (uint32_t j = 0; j < m; ++j) active[j] = j;
-  per_map->assign(m, FKS_OK);
-  maps_out->assign(m, fks_map());
+  per_map.assign(m, FKS_OK);
+  maps.assign(m, fks_map());
+  profile = fks_build_profile{};
   std::vector<uint32_t> exhausted;  // maps whose rounds all failed
   fks_status hard = FKS_OK;         // a failure of the whole call
   std::string hard_msg;
-  const int sms = sm_count();
   ProfileEvents prof;
-  fks_build_profile profile{};
-
-  auto cleanup = [&]() {
-    if (ovf_key) A.put(ovf_key, ovf_bytes, st);
-    A.put(scr, cs.off, st);
-  };
+  bool first = true;
 
   while (!active.empty() && hard == FKS_OK) {
     const uint32_t ma = uint32_t(active.size());
-    // ---- pass tables
-    const size_t up_bytes = sizeof(MapDev) * ma + sizeof(uint64_t) * (ma + 1) + sizeof(uint32_t) * (ma + 1);
-    uint8_t* up = static_cast<uint8_t*>(g_pin_up.get(up_bytes));
-    if (!up) { hard = FKS_ERR_CUDA; hard_msg = "pinned staging"; break; }
-    MapDev* h_maps = reinterpret_cast<MapDev*>(up);
-    uint64_t* h_pseg = reinterpret_cast<uint64_t*>(up + sizeof(MapDev) * ma);
-    uint32_t* h_qseg = reinterpret_cast<uint32_t*>(up + sizeof(MapDev) * ma + sizeof(uint64_t) * (ma + 1));
-    uint64_t pe = 0;
-    uint32_t pp = 0;
-    for (uint32_t a = 0; a < ma; ++a) {
-      const uint32_t j = active[a];
-      const uint64_t n = uint64_t(in.seg[j + 1] - in.seg[j]);
-      MapDev& M = h_maps[a];
-      M.key_begin = uint64_t(in.seg[j]);
-      M.pass_begin = pe;
-      M.desc_base = desc_base[j];
-      M.slot_base = slot_base[j];
-      M.seed = in.seeds[j];
-      M.round = round[j];
-      M.c1 = derive(M.seed, M.round, kTagLevel1, 0);
-      M.fpb = fp_base(M.seed, M.round);
-      M.n = uint32_t(n);
-      M.nb = uint32_t(nbs[j]);
-      M.slot_cap = uint32_t(uint64_t(o.bound) * n);
-      M.part_begin = pp;
-      h_pseg[a] = pe;
-      h_qseg[a] = pp;
-      pe += n;
-      pp += uint32_t((nbs[j] + B - 1) / B);
+    // the first pass of a recorded build is a launch of its graph
+    const bool replay = first && g != nullptr;
+    uint8_t* up = replay ? g->up : static_cast<uint8_t*>(g_pin_up.get(up_bytes(ma)));
+    uint8_t* down = replay ? g->down : static_cast<uint8_t*>(g_pin_down.get(down_bytes(ma)));
+    if (!up || !down) {
+      hard = FKS_ERR_CUDA;
+      hard_msg = "pinned staging";
+      break;
     }
-    h_pseg[ma] = pe;
-    h_qseg[ma] = pp;
-    p.m = ma;
-    p.P = pp;
-    p.total = pe;
+    fill_tables(active, up);
     cudaError_t e;
-#define FKS_PASS(call)                                  \
-  if ((e = (call)) != cudaSuccess) {                    \
-    hard = FKS_ERR_CUDA;                                \
+#define FKS_PASS(call)                                          \
+  if ((e = (call)) != cudaSuccess) {                            \
+    hard = FKS_ERR_CUDA;                                        \
     hard_msg = std::string(#call ": ") + cudaGetErrorString(e); \
-    break;                                              \
+    break;                                                      \
   }
-    FKS_PASS(cudaMemcpyAsync(d_maps, h_maps, sizeof(MapDev) * ma, cudaMemcpyHostToDevice, st));
-    FKS_PASS(cudaMemcpyAsync(d_pseg, h_pseg, sizeof(uint64_t) * (ma + 1), cudaMemcpyHostToDevice, st));
-    FKS_PASS(cudaMemcpyAsync(d_qseg, h_qseg, sizeof(uint32_t) * (ma + 1), cudaMemcpyHostToDevice, st));
-    FKS_PASS(cudaMemsetAsync(d_stat, 0, sizeof(MapStatus) * ma, st));
-    if (prof.ok && str) cudaEventRecord(prof.fp0, st);
-    if (str) FKS_PASS(launch_fingerprints(in.ctx, in.offs, total, d_maps, d_pseg, ma, pe, fps, d_stat, st));
-    if (prof.ok && str) cudaEventRecord(prof.fp1, st);
-    SplitShape sh = split_shape(pp, pe);
-    const bool split_pass = use_split && sh.ok && split_hist_words(sh) <= hist_words &&
-                            sh.binsA <= shape.binsA && pe >= kSplitMinKeys;
-    if (split_pass) {
-      SplitDev sd{};
-      sd.binsA = sh.binsA;
-      sd.binsB = sh.binsB;
-      sd.shiftB = sh.shiftB;
-      sd.tilesA = sh.tilesA;
-      sd.tilesB_max = sh.tilesB_max;
-      sd.histA = sd.histB = reinterpret_cast<uint32_t*>(scr + s_hist);
-      sd.sums = reinterpret_cast<uint32_t*>(scr + s_sums);
-      sd.startA = reinterpret_cast<uint64_t*>(scr + s_sa);
-      sd.tstartB = reinterpret_cast<uint32_t*>(scr + s_tb);
-      sd.keyA = reinterpret_cast<uint64_t*>(scr + s_ka);
-      sd.payA = reinterpret_cast<uint64_t*>(scr + s_pa);
-      sd.gpA = reinterpret_cast<uint32_t*>(scr + s_ga);
-      profile.grouping_levels = 2;
-      FKS_PASS(launch_pass_split(p, sd, str, sms, st, prof.ok ? &prof.pe : nullptr));
+    if (replay) {
+      FKS_PASS(cudaGraphLaunch(g->exec, st));
+      note_launches(g->kernels);
     } else {
-      profile.grouping_levels = 1;
-      FKS_PASS(launch_pass(p, str, sms, st, prof.ok ? &prof.pe : nullptr));
+      FKS_PASS(enqueue_pass(ma, up, down, first, prof.ok ? &prof : nullptr, st));
     }
-    // ---- status
-    const size_t down_bytes = sizeof(MapStatus) * ma + 16;
-    uint8_t* down = static_cast<uint8_t*>(g_pin_down.get(down_bytes));
-    if (!down) { hard = FKS_ERR_CUDA; hard_msg = "pinned staging"; break; }
-    MapStatus* h_stat = reinterpret_cast<MapStatus*>(down);
-    uint32_t* h_ovf = reinterpret_cast<uint32_t*>(down + sizeof(MapStatus) * ma);
-    FKS_PASS(cudaMemcpyAsync(h_stat, d_stat, sizeof(MapStatus) * ma, cudaMemcpyDeviceToHost, st));
-    FKS_PASS(cudaMemcpyAsync(h_ovf, p.ovf_count, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     FKS_PASS(cudaStreamSynchronize(st));
-    prof.accumulate(&profile, str);
-    if (*h_ovf) {
+    if (!replay) {
+      profile.grouping_levels = levels;
+      prof.accumulate(&profile, str);
+    }
+    first = false;
+    MapStatus* h_stat = reinterpret_cast<MapStatus*>(down);
+    const uint32_t h_ovf = *reinterpret_cast<uint32_t*>(down + sizeof(MapStatus) * ma);
+    if (h_ovf) {
       if (!ovf_key) {
         ovf_bytes = sizeof(uint64_t) * (total * (1 + PW) + 2);
         ovf_key = static_cast<uint64_t*>(A.get(ovf_bytes, st));
-        if (!ovf_key) { hard = FKS_ERR_OUT_OF_MEMORY; hard_msg = "overflow buffer"; break; }
+        if (!ovf_key) {
+          hard = FKS_ERR_OUT_OF_MEMORY;
+          hard_msg = "overflow buffer";
+          break;
+        }
       }
       p.ovf_key = ovf_key;
       p.ovf_pay = ovf_key + total;
-      FKS_PASS(launch_overflow(p, str, *h_ovf, st));
+      FKS_PASS(launch_overflow(p, str, h_ovf, st));
       FKS_PASS(cudaMemcpyAsync(h_stat, d_stat, sizeof(MapStatus) * ma, cudaMemcpyDeviceToHost, st));
       FKS_PASS(cudaStreamSynchronize(st));
     }
 #undef FKS_PASS
     // ---- decide per map
+    const MapDev* h_maps = reinterpret_cast<const MapDev*>(up);
     std::vector<uint32_t> next;
     for (uint32_t a = 0; a < ma; ++a) {
       const uint32_t j = active[a];
       const MapStatus& S = h_stat[a];
       if (S.invalid) {
-        (*per_map)[j] = FKS_ERR_INVALID_ARG;
+        per_map[j] = FKS_ERR_INVALID_ARG;
         continue;
       }
       if (S.timeout) {
-        (*per_map)[j] = FKS_ERR_TIMEOUT;
+        per_map[j] = FKS_ERR_TIMEOUT;
         continue;
       }
       bool redo = false;
       if (S.reseed) redo = true;
       else if (S.dup) {
-        (*per_map)[j] = FKS_ERR_DUPLICATE_KEY;
+        per_map[j] = FKS_ERR_DUPLICATE_KEY;
         continue;
       } else if (S.next_round) redo = true;
       if (redo) {
@@ -586,7 +689,7 @@ static fks_status build_impl(const BuildIn& in, const Opts& o, const Alloc& A, c
         }
         continue;
       }
-      fks_map& M = (*maps_out)[j];
+      fks_map& M = maps[j];
       M.kind = in.kind;
       M.vt = in.vt;
       M.n = uint64_t(in.seg[j + 1] - in.seg[j]);
@@ -603,9 +706,9 @@ static fks_status build_impl(const BuildIn& in, const Opts& o, const Alloc& A, c
       M.nonempty = S.nonempty;
       M.nb = nbs[j];
       M.lambda = o.lambda;
-      M.desc = mem->desc + desc_base[j];
-      M.slots = mem->slots + slot_base[j] * W;
-      M.ctx = mem->ctx;
+      M.desc = mem.desc + mem.desc_base[j];
+      M.slots = mem.slots + mem.slot_base[j] * W;
+      M.ctx = mem.ctx;
       M.ctx_bytes = ctx_bytes;
       M.bytes = sizeof(uint64_t) * (M.nb + W * M.slot_cap);
     }
@@ -619,13 +722,17 @@ static fks_status build_impl(const BuildIn& in, const Opts& o, const Alloc& A, c
     while (size < 2 * n) size <<= 1;
     const size_t tb = sizeof(uint64_t) * size + (str ? sizeof(uint32_t) * size : 0) + 64;
     uint8_t* tbl = static_cast<uint8_t*>(A.get(tb, st));
-    if (!tbl) { hard = FKS_ERR_OUT_OF_MEMORY; hard_msg = "duplicate test table"; break; }
+    if (!tbl) {
+      hard = FKS_ERR_OUT_OF_MEMORY;
+      hard_msg = "duplicate test table";
+      break;
+    }
     uint64_t* table = reinterpret_cast<uint64_t*>(tbl);
     uint32_t* tidx = str ? reinterpret_cast<uint32_t*>(tbl + sizeof(uint64_t) * size) : nullptr;
     uint32_t* flags = reinterpret_cast<uint32_t*>(tbl + tb - 64);
     const uint64_t* hk = str ? fps + in.seg[j] : in.keys + in.seg[j];
-    cudaError_t e = launch_dupcheck(hk, str ? in.offs + in.seg[j] : nullptr, in.ctx, n, table, tidx,
-                                    size, flags, o.spin, st);
+    cudaError_t e = launch_dupcheck(hk, str ? in.offs + in.seg[j] : nullptr, in.ctx, n, table, tidx, size, flags,
+                                    o.spin, st);
     uint32_t hf[4] = {0, 0, 0, 0};
     if (e == cudaSuccess) e = cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -635,16 +742,32 @@ static fks_status build_impl(const BuildIn& in, const Opts& o, const Alloc& A, c
       hard_msg = std::string("duplicate test: ") + cudaGetErrorString(e);
       break;
     }
-    (*per_map)[j] = hf[2] ? FKS_ERR_TIMEOUT : (hf[0] ? FKS_ERR_DUPLICATE_KEY : FKS_ERR_BUILD_FAILED);
+    per_map[j] = hf[2] ? FKS_ERR_TIMEOUT : (hf[0] ? FKS_ERR_DUPLICATE_KEY : FKS_ERR_BUILD_FAILED);
   }
-  cleanup();
   if (prof.ok) g_last_profile = profile;
-  if (hard != FKS_OK) {
-    A.put(block, cm.off, st);
-    return fail(hard, hard_msg);
+  if (hard != FKS_OK) return fail(hard, hard_msg);
+  return FKS_OK;
+}
+
+// One-shot build of a set: init, the rounds, scratch released; the tables
+// are handed to the caller.
+static fks_status build_impl(const BuildIn& in, const Opts& o, const Alloc& A, cudaStream_t st,
+                             void** out_block, size_t* out_block_bytes, SetMem* mem,
+                             std::vector<fks_map>* maps_out, std::vector<fks_status>* per_map) {
+  SetBuild b;
+  fks_status s = b.init(in, o, A, st);
+  if (s != FKS_OK) return s;
+  s = b.run(st, nullptr);
+  b.free_scratch(st);
+  if (s != FKS_OK) {
+    b.free_tables(st);
+    return s;
   }
-  *out_block = block;
-  *out_block_bytes = cm.off;
+  *out_block = b.block;
+  *out_block_bytes = b.block_bytes;
+  *mem = b.mem;
+  *maps_out = std::move(b.maps);
+  *per_map = std::move(b.per_map);
   return FKS_OK;
 }
 
@@ -782,6 +905,28 @@ static fks_status build_single(const BuildIn& in, const fks_build_opts* opts,
   return FKS_OK;
 }
 
+// The device table of a set for batched lookups (set->d_table, already
+// allocated): maps that failed keep n = 0 and answer every needle with
+// absent, their first descriptor made an empty bucket.  Synchronises.
+static fks_status publish_set(fks_mapset* set, const SetMem& mem, const std::vector<fks_status>& per,
+                              cudaStream_t st) {
+  const uint32_t m = uint32_t(set->maps.size());
+  std::vector<LookupMap> tab(m);
+  for (uint32_t j = 0; j < m; ++j) {
+    if (per[j] == FKS_OK) tab[j] = lookup_view(set->maps[j]);
+    else {
+      memset(&tab[j], 0, sizeof(LookupMap));
+      tab[j].desc = mem.desc + mem.desc_base[j];
+      tab[j].nb = 1;  // a single empty bucket
+    }
+  }
+  for (uint32_t j = 0; j < m; ++j)
+    if (per[j] != FKS_OK) FKS_CUDA(cudaMemsetAsync(mem.desc + mem.desc_base[j], 0, sizeof(uint64_t), st));
+  FKS_CUDA(cudaMemcpyAsync(set->d_table, tab.data(), sizeof(LookupMap) * m, cudaMemcpyHostToDevice, st));
+  FKS_CUDA(cudaStreamSynchronize(st));
+  return FKS_OK;
+}
+
 // Lookup view of a map handle, for the serving loop (fks_serve.cu).
 namespace fks {
 bool lookup_view_of(fks_map_t m, LookupMap* out, int* strings, int* out_i64) {
@@ -793,6 +938,75 @@ bool lookup_view_of(fks_map_t m, LookupMap* out, int* strings, int* out_i64) {
 }
 int device_sm_count() { return sm_count(); }
 }  // namespace fks
+
+// Arguments of a batched build; the segment offsets (host or device memory)
+// are copied to *seg.
+static fks_status check_batched(const char* who, fks_key_kind kind, const uint64_t* keys, const uint8_t* ctx,
+                                const int64_t* offs, const int64_t* h_seg, uint32_t m, const void* vals,
+                                fks_val_type val_type, std::vector<int64_t>* seg) {
+  const std::string w(who);
+  if (m == 0 || !h_seg || !vals || (val_type != FKS_VAL_I32 && val_type != FKS_VAL_I64))
+    return fail(FKS_ERR_INVALID_ARG, w + ": bad arguments");
+  seg->resize(size_t(m) + 1);
+  cudaPointerAttributes pa{};
+  if (cudaPointerGetAttributes(&pa, h_seg) == cudaSuccess &&
+      (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged)) {
+    FKS_CUDA(cudaMemcpy(seg->data(), h_seg, sizeof(int64_t) * (m + 1), cudaMemcpyDeviceToHost));
+  } else {
+    memcpy(seg->data(), h_seg, sizeof(int64_t) * (m + 1));
+  }
+  cudaGetLastError();
+  const int64_t* s = seg->data();
+  if (kind == FKS_KEY_U64 ? !keys : (kind == FKS_KEY_BYTES ? (!ctx || !offs) : true))
+    return fail(FKS_ERR_INVALID_ARG, w + ": bad key arguments");
+  if (s[0] != 0) return fail(FKS_ERR_INVALID_ARG, w + ": h_seg[0] != 0");
+  for (uint32_t j = 0; j < m; ++j) {
+    const int64_t n = s[j + 1] - s[j];
+    if (n <= 0 || n >= (int64_t(1) << 30)) return fail(FKS_ERR_INVALID_ARG, w + ": empty or oversized segment");
+  }
+  if (uint64_t(s[m]) >= (1ull << 32)) return fail(FKS_ERR_INVALID_ARG, w + ": 2^32 keys or more");
+  return FKS_OK;
+}
+
+// ---------------------------------------------------------------- recorded builds
+// A batched build whose first pass -- every map at level-one round 0 -- is
+// recorded once as a CUDA graph over fixed input buffers and replayed by each
+// run; maps that must redraw finish through the ordinary pass loop.
+struct fks_build_graph {
+  std::mutex mu;
+  SetBuild b;
+  GraphPass gp;
+  cudaGraph_t graph = nullptr;
+  std::vector<int64_t> seg;     // the graph's own copy of the segment offsets
+  std::vector<uint64_t> seeds;  // seeds of the current run
+  fks_mapset set;               // the maps of the last run; tables in b.block
+};
+
+static void graph_release(fks_build_graph* g) {
+  if (g->gp.exec) cudaGraphExecDestroy(g->gp.exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  if (g->gp.up) cudaFreeHost(g->gp.up);
+  if (g->gp.down) cudaFreeHost(g->gp.down);
+  g->b.free_scratch(nullptr);
+  g->b.free_tables(nullptr);
+  if (g->set.d_table) g->b.A.put(g->set.d_table, sizeof(LookupMap) * g->b.m, nullptr);
+  cudaDeviceSynchronize();
+  delete g;
+}
+
+// Kernel nodes of a graph (what one launch of it runs).
+static uint32_t graph_kernels(cudaGraph_t graph) {
+  size_t count = 0;
+  if (cudaGraphGetNodes(graph, nullptr, &count) != cudaSuccess || count == 0) return 0;
+  std::vector<cudaGraphNode_t> nodes(count);
+  if (cudaGraphGetNodes(graph, nodes.data(), &count) != cudaSuccess) return 0;
+  uint32_t k = 0;
+  for (size_t i = 0; i < count; ++i) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++k;
+  }
+  return k;
+}
 
 // ================================================================ C ABI
 extern "C" {
@@ -910,7 +1124,7 @@ fks_status fks_lookup_u64(fks_map_t map, const uint64_t* q, uint64_t nq, void* o
   if (nq == 0) return FKS_OK;
   if (!q || !absent_fits(map, absent)) return fail(FKS_ERR_INVALID_ARG, "fks_lookup_u64: bad arguments");
   FKS_CUDA(launch_lookup_u64(lookup_view(*map), q, nq, out_vals, map->vt == FKS_VAL_I64, out_found,
-                             absent, sm_count(), reinterpret_cast<cudaStream_t>(stream)));
+                             absent, sm_count(), lookup_shape_for(map->lambda), reinterpret_cast<cudaStream_t>(stream)));
   return FKS_OK;
 }
 
@@ -935,30 +1149,12 @@ fks_status fks_build_batched(fks_key_kind kind, const uint64_t* keys, const uint
                              fks_stream_t stream, fks_mapset_t* out, fks_status* h_status) {
   if (!out) return fail(FKS_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
-  if (m == 0 || !h_seg || !h_seeds || !vals || (val_type != FKS_VAL_I32 && val_type != FKS_VAL_I64))
-    return fail(FKS_ERR_INVALID_ARG, "fks_build_batched: bad arguments");
-  // segment offsets in device memory are brought to the host first
+  if (!h_seeds) return fail(FKS_ERR_INVALID_ARG, "fks_build_batched: bad arguments");
   std::vector<int64_t> seg_copy;
-  {
-    cudaPointerAttributes pa{};
-    if (cudaPointerGetAttributes(&pa, h_seg) == cudaSuccess &&
-        (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged)) {
-      seg_copy.resize(size_t(m) + 1);
-      FKS_CUDA(cudaMemcpy(seg_copy.data(), h_seg, sizeof(int64_t) * (m + 1), cudaMemcpyDeviceToHost));
-      h_seg = seg_copy.data();
-    }
-    cudaGetLastError();
-  }
-  if (kind == FKS_KEY_U64 ? !keys : (kind == FKS_KEY_BYTES ? (!ctx || !offs) : true))
-    return fail(FKS_ERR_INVALID_ARG, "fks_build_batched: bad key arguments");
-  if (h_seg[0] != 0) return fail(FKS_ERR_INVALID_ARG, "fks_build_batched: h_seg[0] != 0");
-  for (uint32_t j = 0; j < m; ++j) {
-    const int64_t n = h_seg[j + 1] - h_seg[j];
-    if (n <= 0 || n >= (int64_t(1) << 30))
-      return fail(FKS_ERR_INVALID_ARG, "fks_build_batched: empty or oversized segment");
-  }
-  if (uint64_t(h_seg[m]) >= (1ull << 32))
-    return fail(FKS_ERR_INVALID_ARG, "fks_build_batched: 2^32 keys or more");
+  if (const fks_status cs = check_batched("fks_build_batched", kind, keys, ctx, offs, h_seg, m, vals, val_type,
+                                          &seg_copy))
+    return cs;
+  h_seg = seg_copy.data();
   Opts o;
   if (!read_opts(opts, &o)) return fail(FKS_ERR_INVALID_ARG, "bad build options");
   Alloc A(alloc);
@@ -993,30 +1189,14 @@ fks_status fks_build_batched(fks_key_kind kind, const uint64_t* keys, const uint
   set->block = block;
   set->block_bytes = bb;
   set->alloc = A;
-  // device table for batched lookups (maps that failed keep n = 0: always absent)
-  std::vector<LookupMap> tab(m);
-  for (uint32_t j = 0; j < m; ++j) {
-    if (per[j] == FKS_OK) tab[j] = lookup_view(set->maps[j]);
-    else {
-      memset(&tab[j], 0, sizeof(LookupMap));
-      tab[j].desc = mem.desc + mem.desc_base[j];
-      tab[j].nb = 1;  // a single empty bucket
-    }
-  }
-  // failed maps: make their first descriptor an empty bucket
-  for (uint32_t j = 0; j < m; ++j)
-    if (per[j] != FKS_OK) cudaMemsetAsync(mem.desc + mem.desc_base[j], 0, sizeof(uint64_t), st);
   set->d_table = static_cast<LookupMap*>(A.get(sizeof(LookupMap) * m, st));
   if (!set->d_table) {
     fks_mapset_destroy(set);
     return fail(FKS_ERR_OUT_OF_MEMORY, "lookup table");
   }
-  cudaError_t e = cudaMemcpyAsync(set->d_table, tab.data(), sizeof(LookupMap) * m,
-                                  cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) {
+  if (const fks_status ps = publish_set(set, mem, per, st)) {
     fks_mapset_destroy(set);
-    return cuda_fail(e, "lookup table upload");
+    return ps;
   }
   *out = set;
   if (worst != FKS_OK) g_last_error = std::string("fks_build_batched: ") + status_name(worst);
@@ -1038,6 +1218,108 @@ fks_status fks_lookup_batched(fks_mapset_t set, const uint32_t* map_ids, const u
                                  qoffs, nq, out_vals, set->vt == FKS_VAL_I64, out_found, absent,
                                  sm_count(), reinterpret_cast<cudaStream_t>(stream)));
   return FKS_OK;
+}
+
+fks_status fks_build_graph_create(fks_key_kind kind, const uint64_t* keys, const uint8_t* ctx,
+                                  const int64_t* offs, const int64_t* h_seg, uint32_t m, const void* vals,
+                                  fks_val_type val_type, const fks_build_opts* opts, const fks_allocator* alloc,
+                                  fks_stream_t stream, fks_build_graph_t* out) {
+  if (!out) return fail(FKS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  std::vector<int64_t> seg;
+  if (const fks_status cs = check_batched("fks_build_graph_create", kind, keys, ctx, offs, h_seg, m, vals,
+                                          val_type, &seg))
+    return cs;
+  Opts o;
+  if (!read_opts(opts, &o)) return fail(FKS_ERR_INVALID_ARG, "bad build options");
+  if (o.dedup) return fail(FKS_ERR_INVALID_ARG, "fks_build_graph_create: dedup changes the sizes; not recordable");
+  const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  sm_count();
+  fks_build_graph* g = new fks_build_graph();
+  g->seg = std::move(seg);
+  g->seeds.assign(m, 0);
+  const BuildIn in{kind, keys, ctx, offs, vals, val_type, m, g->seg.data(), g->seeds.data()};
+  fks_status s = g->b.init(in, o, Alloc(alloc), st);
+  if (s != FKS_OK) {
+    delete g;
+    return s;
+  }
+  SetBuild& b = g->b;
+  g->set.kind = kind;
+  g->set.vt = val_type;
+  g->set.alloc = b.A;
+  g->set.borrowed = true;
+  g->set.maps.assign(m, fks_map());
+  g->set.d_table = static_cast<LookupMap*>(b.A.get(sizeof(LookupMap) * m, st));
+  if (!g->set.d_table || cudaMallocHost(&g->gp.up, SetBuild::up_bytes(m)) != cudaSuccess ||
+      cudaMallocHost(&g->gp.down, SetBuild::down_bytes(m)) != cudaSuccess) {
+    cudaGetLastError();
+    graph_release(g);
+    return fail(FKS_ERR_OUT_OF_MEMORY, "fks_build_graph_create: tables or pinned buffers");
+  }
+  // record the first pass on a stream of our own (the caller's may be the
+  // legacy default stream, which cannot capture)
+  b.round.assign(m, 0);
+  std::vector<uint32_t> all(m);
+  for (uint32_t j = 0; j < m; ++j) all[j] = j;
+  b.fill_tables(all, g->gp.up);
+  cudaStream_t cap = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // allocations above are ordered on `st`
+  if (e == cudaSuccess) {
+    const uint64_t before = g_launches.load();
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+      const cudaError_t ep = b.enqueue_pass(m, g->gp.up, g->gp.down, true, nullptr, cap);
+      e = cudaStreamEndCapture(cap, &g->graph);
+      if (ep != cudaSuccess) e = ep;
+    }
+    g_launches.fetch_sub(g_launches.load() - before);  // recorded, not launched
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&g->gp.exec, g->graph, 0);
+  if (cap) cudaStreamDestroy(cap);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    graph_release(g);
+    return cuda_fail(e, "fks_build_graph_create: recording the first pass");
+  }
+  g->gp.kernels = graph_kernels(g->graph);
+  *out = g;
+  return FKS_OK;
+}
+
+fks_status fks_build_graph_run(fks_build_graph_t g, const uint64_t* h_seeds, fks_stream_t stream,
+                               fks_status* h_status) {
+  if (!g || !h_seeds) return fail(FKS_ERR_INVALID_ARG, "fks_build_graph_run: NULL argument");
+  std::lock_guard<std::mutex> lock(g->mu);
+  const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  SetBuild& b = g->b;
+  const uint32_t m = b.m;
+  memcpy(g->seeds.data(), h_seeds, sizeof(uint64_t) * m);
+  fks_status s = b.run(st, &g->gp);
+  if (s != FKS_OK) {
+    for (uint32_t j = 0; j < m; ++j) g->set.maps[j] = fks_map();
+    return s;
+  }
+  fks_status worst = FKS_OK;
+  for (uint32_t j = 0; j < m; ++j) {
+    g->set.maps[j] = b.maps[j];  // element-wise: handles from fks_mapset_get stay put
+    if (h_status) h_status[j] = b.per_map[j];
+    if (b.per_map[j] != FKS_OK && worst == FKS_OK) worst = b.per_map[j];
+  }
+  if (const fks_status ps = publish_set(&g->set, b.mem, b.per_map, st)) return ps;
+  if (worst != FKS_OK) g_last_error = std::string("fks_build_graph_run: ") + status_name(worst);
+  return worst;
+}
+
+fks_mapset_t fks_build_graph_mapset(fks_build_graph_t g) { return g ? &g->set : nullptr; }
+
+uint32_t fks_build_graph_kernels(fks_build_graph_t g) { return g ? g->gp.kernels : 0u; }
+
+void fks_build_graph_destroy(fks_build_graph_t g) {
+  if (!g) return;
+  { std::lock_guard<std::mutex> lock(g->mu); }  // a run on another thread finishes first
+  graph_release(g);
 }
 
 uint32_t fks_mapset_size(fks_mapset_t set) { return set ? uint32_t(set->maps.size()) : 0u; }
@@ -1101,7 +1383,7 @@ void fks_map_destroy(fks_map_t map) {
 }
 
 void fks_mapset_destroy(fks_mapset_t set) {
-  if (!set) return;
+  if (!set || set->borrowed) return;
   if (set->d_table) set->alloc.put(set->d_table, sizeof(LookupMap) * set->maps.size(), nullptr);
   if (set->block) set->alloc.put(set->block, set->block_bytes, nullptr);
   delete set;

@@ -1183,7 +1183,7 @@ cudaError_t launch_fingerprints(const uint8_t* ctx, const int64_t* offs, uint64_
 }
 
 template <int PW>
-static cudaError_t launch_build_kernel(const PassDev& p, int sms, cudaStream_t stream) {
+static cudaError_t launch_build_kernel(const PassDev& p, int sms, const BuildShape& shape, cudaStream_t stream) {
   static int occ = -1;
   const int smem = int(Smem<PW>::kBytes);
   if (occ < 0) {
@@ -1198,13 +1198,14 @@ static cudaError_t launch_build_kernel(const PassDev& p, int sms, cudaStream_t s
     if (e != cudaSuccess) return e;
     occ = o > 0 ? o : 1;
   }
-  const uint64_t want = uint64_t(sms) * occ;
+  const uint64_t per_sm = shape.part_ctas_per_sm && int(shape.part_ctas_per_sm) < occ ? shape.part_ctas_per_sm : occ;
+  const uint64_t want = uint64_t(sms) * per_sm;
   const unsigned grid = unsigned(p.P < want ? p.P : want);
   k_part_build<PW><<<grid, kPartThreads, smem, stream>>>(p);
   return cudaGetLastError();
 }
 
-cudaError_t launch_pass(const PassDev& p, bool strings, int sms, cudaStream_t stream,
+cudaError_t launch_pass(const PassDev& p, bool strings, int sms, const BuildShape& shape, cudaStream_t stream,
                         const PassEvents* ev) {
   if (p.total == 0 || p.P == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(p.part_cnt, 0, sizeof(uint32_t) * p.P, stream);
@@ -1214,7 +1215,7 @@ cudaError_t launch_pass(const PassDev& p, bool strings, int sms, cudaStream_t st
   const int agg = (p.total / p.P) < 64 || p.P < 64 ? 1 : 0;
   const size_t seg_smem = (p.m > 1 && p.m <= 2048) ? sizeof(uint64_t) * (p.m + 1) : 0;
   uint64_t blocks = (p.total + 256 * kUnroll - 1) / (256 * kUnroll);
-  const uint64_t maxb = uint64_t(sms) * 8;
+  const uint64_t maxb = uint64_t(sms) * (shape.scatter_blocks_per_sm ? shape.scatter_blocks_per_sm : 8u);
   if (blocks > maxb) blocks = maxb;
   if (strings) k_partition<false, true><<<unsigned(blocks), 256, seg_smem, stream>>>(p, agg);
   else k_partition<false, false><<<unsigned(blocks), 256, seg_smem, stream>>>(p, agg);
@@ -1227,14 +1228,14 @@ cudaError_t launch_pass(const PassDev& p, bool strings, int sms, cudaStream_t st
   else k_partition<true, false><<<unsigned(blocks), 256, seg_smem, stream>>>(p, agg);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev->ev[3], stream);
-  e = strings ? launch_build_kernel<2>(p, sms, stream) : launch_build_kernel<1>(p, sms, stream);
+  e = strings ? launch_build_kernel<2>(p, sms, shape, stream) : launch_build_kernel<1>(p, sms, shape, stream);
   if (e != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev->ev[4], stream);
   note_launches(4);
   return cudaSuccess;
 }
 
-cudaError_t launch_pass_split(const PassDev& p, const SplitDev& s, bool strings, int sms,
+cudaError_t launch_pass_split(const PassDev& p, const SplitDev& s, bool strings, int sms, const BuildShape& shape,
                               cudaStream_t stream, const PassEvents* ev) {
   if (p.total == 0 || p.P == 0) return cudaSuccess;
   if (ev) cudaEventRecord(ev->ev[0], stream);
@@ -1245,7 +1246,7 @@ cudaError_t launch_pass_split(const PassDev& p, const SplitDev& s, bool strings,
     cudaEventRecord(ev->ev[2], stream);
     cudaEventRecord(ev->ev[3], stream);
   }
-  e = strings ? launch_build_kernel<2>(p, sms, stream) : launch_build_kernel<1>(p, sms, stream);
+  e = strings ? launch_build_kernel<2>(p, sms, shape, stream) : launch_build_kernel<1>(p, sms, shape, stream);
   if (e != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev->ev[4], stream);
   note_launches(1);

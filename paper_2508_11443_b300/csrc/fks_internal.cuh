@@ -117,6 +117,28 @@ struct PassDev {
 // Process-wide count of kernels launched by the library (fks_api.cu).
 void note_launches(uint32_t n);
 
+// Launch shapes of a build and of a uint64 lookup: the defaults below, or
+// what fks_autotune measured best for a (key kind, keys per bucket) pair
+// (fks_tune.cu).  No shape changes a table or a result: every shape runs
+// the same steps and keeps the first successful attempt of every bucket.
+struct BuildShape {
+  uint32_t thread_max;             // buckets of 2 .. thread_max keys are searched by one thread each
+  uint32_t part_ctas_per_sm;       // partition-build CTAs per SM (capped by occupancy)
+  uint32_t scatter_blocks_per_sm;  // grid of the one-level count / scatter kernels
+  uint32_t split_min_log2;         // passes of >= 2^x keys are grouped in two radix levels
+};
+struct LookupShape {
+  uint32_t queries_per_thread;  // 2, 4 or 8 needles in flight per thread
+  uint32_t block;               // 128, 256 or 512 threads
+  uint32_t blocks_per_sm;       // grid = SMs x this (grid-stride loop)
+};
+BuildShape default_build_shape(uint32_t lambda);
+LookupShape default_lookup_shape();
+// The shape a build / lookup uses: a thread's override (set while the
+// autotuner measures candidates), else the tuned table, else the default.
+BuildShape build_shape_for(int key_kind, uint32_t lambda);
+LookupShape lookup_shape_for(uint32_t lambda);
+
 // Optional CUDA events recorded between the phases of a pass:
 // ev[0] before counting, ev[1] after counting, ev[2] after the scan,
 // ev[3] after the scatter, ev[4] after the partition build.
@@ -174,11 +196,11 @@ cudaError_t launch_fingerprints(const uint8_t* ctx, const int64_t* offs, uint64_
                                 const MapDev* maps, const uint64_t* pass_seg, uint32_t m,
                                 uint64_t total, uint64_t* fps, MapStatus* status,
                                 cudaStream_t stream);
-cudaError_t launch_pass(const PassDev& p, bool strings, int sms, cudaStream_t stream,
+cudaError_t launch_pass(const PassDev& p, bool strings, int sms, const BuildShape& shape, cudaStream_t stream,
                         const PassEvents* events);
 // The same pass with the keys grouped by launch_split instead of the
 // single-level partition scatter.
-cudaError_t launch_pass_split(const PassDev& p, const SplitDev& s, bool strings, int sms,
+cudaError_t launch_pass_split(const PassDev& p, const SplitDev& s, bool strings, int sms, const BuildShape& shape,
                               cudaStream_t stream, const PassEvents* events);
 cudaError_t launch_overflow(const PassDev& p, bool strings, uint32_t count, cudaStream_t stream);
 cudaError_t launch_dupcheck(const uint64_t* hkeys, const int64_t* offs, const uint8_t* ctx,
@@ -198,7 +220,7 @@ struct LookupMap {
 };
 cudaError_t launch_lookup_u64(const LookupMap& M, const uint64_t* q, uint64_t nq, void* out,
                               int out_i64, uint8_t* found, int64_t absent, int sms,
-                              cudaStream_t stream);
+                              const LookupShape& shape, cudaStream_t stream);
 cudaError_t launch_lookup_bytes(const LookupMap& M, const uint8_t* qctx, const int64_t* qoffs,
                                 uint64_t nq, void* out, int out_i64, uint8_t* found,
                                 int64_t absent, int sms, cudaStream_t stream);

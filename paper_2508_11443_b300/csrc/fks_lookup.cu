@@ -56,12 +56,11 @@ __device__ __forceinline__ ulonglong4 ld_na_u256(const uint64_t* p, uint64_t pol
   return v;
 }
 
-template <int kQ, bool kI64>
-__global__ void __launch_bounds__(kLookupThreads) k_lookup_u64(LookupMap M,
-                                                               const uint64_t* __restrict__ q,
-                                                               uint64_t nq, void* __restrict__ out,
-                                                               uint8_t* __restrict__ found,
-                                                               int64_t absent, int vec) {
+template <int kQ, bool kI64, int NT>
+__global__ void __launch_bounds__(NT) k_lookup_u64(LookupMap M, const uint64_t* __restrict__ q, uint64_t nq,
+                                                   void* __restrict__ out, uint8_t* __restrict__ found,
+                                                   int64_t absent, int vec) {
+  static_assert(kQ == 2 || kQ == 4 || kQ == 8, "2, 4 or 8 needles per thread");
   const uint64_t stride = uint64_t(gridDim.x) * blockDim.x * kQ;
   const uint64_t keep = policy_keep(), strm = policy_stream();
   for (uint64_t base = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) * kQ; base < nq;
@@ -98,12 +97,12 @@ __global__ void __launch_bounds__(kLookupThreads) k_lookup_u64(LookupMap M,
       }
     }
     int64_t v[kQ];
-    uint32_t f = 0;
+    uint64_t f = 0;
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
       const bool hit = sl[i].x == k[i];
       v[i] = hit ? int64_t(sl[i].y) : absent;
-      f |= uint32_t(hit) << (8 * i);
+      f |= uint64_t(hit) << (8 * i);
     }
     if (full) {
       if (out) {
@@ -112,18 +111,19 @@ __global__ void __launch_bounds__(kLookupThreads) k_lookup_u64(LookupMap M,
           for (int i = 0; i < kQ; i += 2)
             __stcs(reinterpret_cast<longlong2*>(static_cast<int64_t*>(out) + base + i),
                    make_longlong2(v[i], v[i + 1]));
+        } else if (kQ == 2) {
+          __stcs(reinterpret_cast<int2*>(static_cast<int32_t*>(out) + base), make_int2(int(v[0]), int(v[1])));
         } else {
 #pragma unroll
           for (int i = 0; i < kQ; i += 4)
             __stcs(reinterpret_cast<int4*>(static_cast<int32_t*>(out) + base + i),
-                   make_int4(int(v[i]), int(v[i + 1]), int(v[i + 2]), int(v[i + 3])));
+                   make_int4(int(v[i]), int(v[i + 1]), int(v[i + 2 < kQ ? i + 2 : 0]), int(v[i + 3 < kQ ? i + 3 : 0])));
         }
       }
       if (found) {
-        if (kQ == 4) __stcs(reinterpret_cast<unsigned int*>(found + base), f);
-        else
-#pragma unroll
-          for (int i = 0; i < kQ; ++i) found[base + i] = uint8_t(f >> (8 * i));
+        if (kQ == 2) __stcs(reinterpret_cast<unsigned short*>(found + base), static_cast<unsigned short>(f));
+        else if (kQ == 4) __stcs(reinterpret_cast<unsigned int*>(found + base), static_cast<unsigned int>(f));
+        else __stcs(reinterpret_cast<unsigned long long*>(found + base), static_cast<unsigned long long>(f));
       }
     } else {
 #pragma unroll
@@ -309,18 +309,39 @@ unsigned grid_for(uint64_t work, int sms, int per_sm) {
 
 }  // namespace
 
+template <int kQ, int NT>
+static void lookup_u64_at(const LookupMap& M, const uint64_t* q, uint64_t nq, void* out, int out_i64, uint8_t* found,
+                          int64_t absent, int vec, unsigned grid, cudaStream_t stream) {
+  if (out_i64) k_lookup_u64<kQ, true, NT><<<grid, NT, 0, stream>>>(M, q, nq, out, found, absent, vec);
+  else k_lookup_u64<kQ, false, NT><<<grid, NT, 0, stream>>>(M, q, nq, out, found, absent, vec);
+}
+
+template <int kQ>
+static void lookup_u64_q(const LookupMap& M, const uint64_t* q, uint64_t nq, void* out, int out_i64, uint8_t* found,
+                         int64_t absent, int vec, uint32_t block, unsigned grid, cudaStream_t stream) {
+  if (block == 128) lookup_u64_at<kQ, 128>(M, q, nq, out, out_i64, found, absent, vec, grid, stream);
+  else if (block == 512) lookup_u64_at<kQ, 512>(M, q, nq, out, out_i64, found, absent, vec, grid, stream);
+  else lookup_u64_at<kQ, 256>(M, q, nq, out, out_i64, found, absent, vec, grid, stream);
+}
+
 cudaError_t launch_lookup_u64(const LookupMap& M, const uint64_t* q, uint64_t nq, void* out,
                               int out_i64, uint8_t* found, int64_t absent, int sms,
-                              cudaStream_t stream) {
+                              const LookupShape& shape, cudaStream_t stream) {
   if (nq == 0) return cudaSuccess;
-  constexpr int kQ = 4;
+  const uint32_t kq = shape.queries_per_thread == 2 || shape.queries_per_thread == 8 ? shape.queries_per_thread : 4u;
+  const uint32_t block = shape.block == 128 || shape.block == 512 ? shape.block : 256u;
+  const uint32_t per_sm = shape.blocks_per_sm ? shape.blocks_per_sm : 8u;
+  // vector loads and stores need 16-byte aligned needles, values and flags
   const int vec = ((reinterpret_cast<uintptr_t>(q) | reinterpret_cast<uintptr_t>(out) |
                     reinterpret_cast<uintptr_t>(found)) & 15u) == 0;
-  const unsigned grid = grid_for((nq + kQ - 1) / kQ, sms, 8);
-  if (out_i64)
-    k_lookup_u64<kQ, true><<<grid, kLookupThreads, 0, stream>>>(M, q, nq, out, found, absent, vec);
-  else
-    k_lookup_u64<kQ, false><<<grid, kLookupThreads, 0, stream>>>(M, q, nq, out, found, absent, vec);
+  const uint64_t threads = (nq + kq - 1) / kq;
+  uint64_t blocks = (threads + block - 1) / block;
+  const uint64_t cap = uint64_t(sms) * per_sm;
+  if (blocks > cap) blocks = cap;
+  const unsigned grid = unsigned(blocks ? blocks : 1);
+  if (kq == 2) lookup_u64_q<2>(M, q, nq, out, out_i64, found, absent, vec, block, grid, stream);
+  else if (kq == 8) lookup_u64_q<8>(M, q, nq, out, out_i64, found, absent, vec, block, grid, stream);
+  else lookup_u64_q<4>(M, q, nq, out, out_i64, found, absent, vec, block, grid, stream);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -201,7 +201,7 @@ extern "C" fks_status fks_build_u64_noalloc(const uint64_t* keys, const void* va
     M.slot_cap = uint32_t(uint64_t(bound) * n);
     NOALLOC_CUDA(cudaMemcpyAsync(d_maps, &M, sizeof(M), cudaMemcpyHostToDevice, s));
     NOALLOC_CUDA(cudaMemsetAsync(d_stat, 0, sizeof(MapStatus), s));
-    NOALLOC_CUDA(launch_pass(p, false, sms, s, nullptr));
+    NOALLOC_CUDA(launch_pass(p, false, sms, default_build_shape(1), s, nullptr));
     NOALLOC_CUDA(cudaMemcpyAsync(&h_stat, d_stat, sizeof(h_stat), cudaMemcpyDeviceToHost, s));
     NOALLOC_CUDA(cudaMemcpyAsync(&h_ovf, p.ovf_count, sizeof(h_ovf), cudaMemcpyDeviceToHost, s));
     NOALLOC_CUDA(cudaStreamSynchronize(s));

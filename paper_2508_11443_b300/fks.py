@@ -175,9 +175,10 @@ class Map:
 
 
 class MapSet:
-    def __init__(self, handle: int, status: np.ndarray):
+    def __init__(self, handle: int, status: np.ndarray, owned: bool = True):
         self.handle = handle
         self.status = status
+        self._owned = owned  # False: the set of a recorded build, freed with it
 
     def __len__(self):
         return int(lib().fks_mapset_size(self.handle))
@@ -187,7 +188,7 @@ class MapSet:
         return Map(h, owner=self) if h else None
 
     def __del__(self):
-        if self.handle and _lib is not None:
+        if self._owned and self.handle and _lib is not None:
             _lib.fks_mapset_destroy(self.handle)
             self.handle = None
 
@@ -307,6 +308,147 @@ def fks_lookup_batched(s: MapSet, map_ids, q=None, qctx=None, qoffs=None, out_va
     nq = map_ids.numel()
     _check(lib().fks_lookup_batched(s.handle, _ptr(map_ids), _ptr(q), _ptr(qctx), _ptr(qoffs), nq,
                                     _ptr(out_vals), _ptr(out_found), absent, _stream(stream)))
+
+
+class BuildGraph:
+    """Owning handle of a recorded batched build (fks_build_graph_*).  Keeps
+    its input tensors alive: the graph reads them on every run."""
+
+    def __init__(self, handle: int, inputs, m: int):
+        self.handle, self._inputs, self.m = handle, inputs, m
+        self.status = np.zeros(m, np.int32)
+
+    def mapset(self) -> MapSet:
+        """The maps of the last run (owned by the graph)."""
+        h = _graph_lib().fks_build_graph_mapset(self.handle)
+        s = MapSet(h, self.status, owned=False)
+        s._graph = self  # the graph must outlive the set's use
+        return s
+
+    def kernels(self) -> int:
+        return int(_graph_lib().fks_build_graph_kernels(self.handle))
+
+    def close(self):
+        if self.handle and _lib is not None:
+            _lib.fks_build_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+
+def _graph_lib():
+    L = lib()
+    if not getattr(L, "_graph_types", False):
+        vp = ctypes.c_void_p
+        L.fks_build_graph_create.argtypes = [ctypes.c_int, vp, vp, vp, vp, ctypes.c_uint32, vp, ctypes.c_int, vp,
+                                             vp, vp, ctypes.POINTER(vp)]
+        L.fks_build_graph_create.restype = ctypes.c_int
+        L.fks_build_graph_run.argtypes = [vp, vp, vp, vp]
+        L.fks_build_graph_run.restype = ctypes.c_int
+        L.fks_build_graph_mapset.argtypes = [vp]
+        L.fks_build_graph_mapset.restype = vp
+        L.fks_build_graph_kernels.argtypes = [vp]
+        L.fks_build_graph_kernels.restype = ctypes.c_uint32
+        L.fks_build_graph_destroy.argtypes = [vp]
+        L.fks_build_graph_destroy.restype = None
+        L._graph_types = True
+    return L
+
+
+def fks_build_graph_create(kind: int, keys, ctx, offs, seg: np.ndarray, vals,
+                           opts: fks_build_opts | None = None, stream=None) -> BuildGraph:
+    seg = np.ascontiguousarray(seg, np.int64)
+    m = seg.size - 1
+    h = ctypes.c_void_p()
+    _check(_graph_lib().fks_build_graph_create(kind, _ptr(keys), _ptr(ctx), _ptr(offs),
+                                               seg.ctypes.data_as(ctypes.c_void_p), m, _ptr(vals),
+                                               _val_type(vals), ctypes.byref(opts) if opts else None, None,
+                                               _stream(stream), ctypes.byref(h)))
+    return BuildGraph(h.value, (keys, ctx, offs, vals), m)
+
+
+def fks_build_graph_run(g: BuildGraph, seeds: np.ndarray, stream=None, raise_on_error=True) -> np.ndarray:
+    """Rebuild every map of the graph with these seeds; per-map statuses."""
+    seeds = np.ascontiguousarray(seeds, np.uint64)
+    assert seeds.size == g.m
+    st = _graph_lib().fks_build_graph_run(g.handle, seeds.ctypes.data_as(ctypes.c_void_p), _stream(stream),
+                                          g.status.ctypes.data_as(ctypes.c_void_p))
+    if raise_on_error:
+        _check(st)
+    return g.status.copy()
+
+
+class fks_tuning(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_size_t), ("key_kind", ctypes.c_uint32),
+                ("keys_per_bucket", ctypes.c_uint32), ("thread_search_max", ctypes.c_uint32),
+                ("part_ctas_per_sm", ctypes.c_uint32), ("scatter_blocks_per_sm", ctypes.c_uint32),
+                ("split_min_keys_log2", ctypes.c_uint32), ("lookup_queries_per_thread", ctypes.c_uint32),
+                ("lookup_block", ctypes.c_uint32), ("lookup_blocks_per_sm", ctypes.c_uint32),
+                ("tuned", ctypes.c_uint32), ("build_ms", ctypes.c_float), ("lookup_ms", ctypes.c_float),
+                ("sample_keys", ctypes.c_uint64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "struct_size"}
+
+
+class fks_tune_trial(ctypes.Structure):
+    _fields_ = [("param", ctypes.c_uint32), ("value", ctypes.c_uint32), ("ms", ctypes.c_float)]
+
+
+TUNE_PARAMS = ("thread_search_max", "part_ctas_per_sm", "scatter_blocks_per_sm", "split_min_keys_log2",
+               "lookup_queries_per_thread<<16|lookup_block", "lookup_blocks_per_sm")
+
+
+def _tune_lib():
+    L = lib()
+    if not getattr(L, "_tune_types", False):
+        vp = ctypes.c_void_p
+        L.fks_autotune.argtypes = [ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                   vp, ctypes.POINTER(fks_tuning), vp, ctypes.c_uint32,
+                                   ctypes.POINTER(ctypes.c_uint32)]
+        L.fks_autotune.restype = ctypes.c_int
+        L.fks_tuning_get.argtypes = [ctypes.c_int, ctypes.c_uint32, ctypes.POINTER(fks_tuning)]
+        L.fks_tuning_get.restype = ctypes.c_int
+        L.fks_tuning_set.argtypes = [ctypes.POINTER(fks_tuning)]
+        L.fks_tuning_set.restype = ctypes.c_int
+        L.fks_tuning_reset.argtypes = []
+        L.fks_tuning_reset.restype = None
+        L._tune_types = True
+    return L
+
+
+def fks_autotune(kind: int = FKS_KEY_U64, keys_per_bucket: int = 1, n: int = 0, nq: int = 0, seed: int = 1,
+                 stream=None):
+    """Measure the launch shapes on a synthetic sample; (entry, trials)."""
+    t = fks_tuning()
+    trials = (fks_tune_trial * 256)()
+    count = ctypes.c_uint32()
+    st = _tune_lib().fks_autotune(kind, keys_per_bucket, n, nq, seed & (2**64 - 1), _stream(stream),
+                                  ctypes.byref(t), ctypes.cast(trials, ctypes.c_void_p), 256, ctypes.byref(count))
+    if st != FKS_OK:
+        raise FksError(st, fks_status_str(st))
+    rows = [(TUNE_PARAMS[trials[i].param], trials[i].value, trials[i].ms) for i in range(min(count.value, 256))]
+    return t, rows
+
+
+def fks_tuning_get(kind: int = FKS_KEY_U64, keys_per_bucket: int = 1) -> fks_tuning:
+    t = fks_tuning()
+    st = _tune_lib().fks_tuning_get(kind, keys_per_bucket, ctypes.byref(t))
+    if st != FKS_OK:
+        raise FksError(st, fks_status_str(st))
+    return t
+
+
+def fks_tuning_set(t: fks_tuning):
+    t.struct_size = ctypes.sizeof(fks_tuning)
+    st = _tune_lib().fks_tuning_set(ctypes.byref(t))
+    if st != FKS_OK:
+        raise FksError(st, fks_status_str(st))
+
+
+def fks_tuning_reset():
+    _tune_lib().fks_tuning_reset()
 
 
 def fks_build_u64_noalloc(keys, vals, seed: int, desc_out, slots_out,

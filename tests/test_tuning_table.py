@@ -1,0 +1,55 @@
+"""The launch-shape table of the autotuner: defaults, validation, install and
+reset (host logic only; no GPU call)."""
+import pytest
+
+from paper_2508_11443_b300 import build as B
+
+
+@pytest.fixture(scope="module")
+def F():
+    B.build()
+    from paper_2508_11443_b300 import fks
+    yield fks
+    fks.fks_tuning_reset()
+
+
+def test_defaults(F):
+    F.fks_tuning_reset()
+    t = F.fks_tuning_get(F.FKS_KEY_U64, 1)
+    assert (t.thread_search_max, t.part_ctas_per_sm, t.scatter_blocks_per_sm, t.split_min_keys_log2) == (3, 0, 8, 20)
+    assert (t.lookup_queries_per_thread, t.lookup_block, t.lookup_blocks_per_sm) == (4, 256, 8)
+    assert t.tuned == 0
+    # with 8 or 16 keys per bucket every bucket of two or more keys goes to a warp segment
+    assert F.fks_tuning_get(F.FKS_KEY_BYTES, 16).thread_search_max == 1
+
+
+def test_install_and_reset(F):
+    F.fks_tuning_reset()
+    t = F.fks_tuning_get(F.FKS_KEY_U64, 4)
+    t.thread_search_max, t.lookup_block, t.lookup_queries_per_thread = 2, 512, 8
+    F.fks_tuning_set(t)
+    got = F.fks_tuning_get(F.FKS_KEY_U64, 4)
+    assert (got.thread_search_max, got.lookup_block, got.lookup_queries_per_thread) == (2, 512, 8)
+    # other (kind, lambda) entries keep their defaults
+    assert F.fks_tuning_get(F.FKS_KEY_U64, 1).thread_search_max == 3
+    assert F.fks_tuning_get(F.FKS_KEY_BYTES, 4).lookup_block == 256
+    F.fks_tuning_reset()
+    assert F.fks_tuning_get(F.FKS_KEY_U64, 4).thread_search_max == 3
+
+
+@pytest.mark.parametrize("field,value", [("thread_search_max", 0), ("thread_search_max", 4),
+                                         ("part_ctas_per_sm", 3), ("scatter_blocks_per_sm", 0),
+                                         ("split_min_keys_log2", 9), ("lookup_queries_per_thread", 3),
+                                         ("lookup_block", 1024), ("lookup_blocks_per_sm", 0),
+                                         ("keys_per_bucket", 3), ("key_kind", 2)])
+def test_out_of_range_entries_are_rejected(F, field, value):
+    t = F.fks_tuning_get(F.FKS_KEY_U64, 1)
+    setattr(t, field, value)
+    with pytest.raises(F.FksError) as e:
+        F.fks_tuning_set(t)
+    assert e.value.status == F.FKS_ERR_INVALID_ARG
+
+
+def test_bad_keys_per_bucket_is_rejected(F):
+    with pytest.raises(F.FksError):
+        F.fks_tuning_get(F.FKS_KEY_U64, 3)
