@@ -271,10 +271,10 @@ def _timed(torch, stream, fn, reps=3, warm=1):
     return statistics.median(ts)
 
 
-def run_strings(F, W, torch, hbm):
+def run_strings(F, W, torch, hbm, shift=0):
     """Config 3: 2^22 distinct strings (lengths uniform in [4, 64], a-z) with
     int32 values; 2^24 needles, 50 % members."""
-    w = W.string_workload(1 << 22, 1 << 24, 0.5, seed=3)
+    w = W.string_workload(1 << (22 - shift), 1 << (24 - shift), 0.5, seed=3)
     ctx, offs = torch.from_numpy(w.ctx).cuda(), torch.from_numpy(w.offs).cuda()
     vals = torch.from_numpy(w.vals.astype(np.int32)).cuda()
     qctx, qoffs = torch.from_numpy(w.qctx).cuda(), torch.from_numpy(w.qoffs).cuda()
@@ -302,10 +302,10 @@ def run_strings(F, W, torch, hbm):
             "results_match_truth": bool(ok), "S_over_n": info.slots / info.n}
 
 
-def run_batched(F, W, torch, hbm):
+def run_batched(F, W, torch, hbm, shift=0):
     """Config 4: 1024 maps of log-uniform size in [16, 2^20] built by one
     batched call; 2^24 (map_id, key) lookups at 75 % hits."""
-    b = W.batched_workload(1024, 16, 1 << 20, 1 << 24, 0.75, seed=4)
+    b = W.batched_workload(1024 >> shift, 16, 1 << (20 - shift), 1 << (24 - shift), 0.75, seed=4)
     keys = torch.from_numpy(b.keys.view(np.int64)).cuda()
     vals = torch.from_numpy(b.vals).cuda()
     ids = torch.from_numpy(b.q_map.astype(np.int32)).cuda()
@@ -320,11 +320,58 @@ def run_batched(F, W, torch, hbm):
     lms = _timed(torch, stream, lambda: F.fks_lookup_batched(S, ids, q=q, out_vals=out, out_found=found))
     ok = np.array_equal(found.cpu().numpy(), b.expect_found)
     lq = 4 + 8 + 32 + 32 * (0.75 + 0.25 * 0.632) + 8 + 1
-    return {"workload": "1024 maps, n log-uniform in [16, 2^20] (sum %d keys); 2^24 lookups, 75%% hits" % total,
+    return {"workload": "%d maps, n log-uniform in [16, 2^%d] (sum %d keys); 2^%d lookups, 75%% hits" % (
+                1024 >> shift, 20 - shift, total, 24 - shift),
             "build_ms": bms, "build_keys_per_s": total / (bms / 1e3), "lookup_ms": lms,
             "lookups_per_s": q.numel() / (lms / 1e3), "lookup_bytes_model": f"{lq:.1f} B/query",
             "lookup_GBps": lq * q.numel() / (lms / 1e3) / 1e9,
             "lookup_frac": lq * q.numel() / (lms / 1e3) / 1e9 / hbm, "results_match_truth": bool(ok)}
+
+
+def run_graph_builds(F, W, torch, shift=0):
+    """Batched builds as one recorded CUDA graph (fks_build_graph_run) against
+    the same batched build launched pass by pass (fks_build_batched) and, for
+    small maps, against one fks_build_u64 call per map: config 4's 1024 maps
+    of log-uniform size in [16, 2^20], and 2048 small maps of log-uniform size
+    in [16, 4096], where launch and synchronisation costs dominate."""
+    stream = torch.cuda.current_stream()
+    res = {}
+    for name, m, lo, hi, per_call in (("config4_1024_maps", 1024 >> shift, 16, 1 << (20 - shift), False),
+                                      ("small_2048_maps", 2048 >> shift, 16, 4096, True)):
+        b = W.batched_workload(m, lo, hi, 16, 0.75, seed=4)
+        keys = torch.from_numpy(b.keys.view(np.int64)).cuda()
+        vals = torch.from_numpy(b.vals).cuda()
+        total = int(b.seg_offs[-1])
+        bms = _timed(torch, stream, lambda: F.fks_build_batched(F.FKS_KEY_U64, keys, None, None, b.seg_offs,
+                                                                  b.seeds, vals), reps=5)
+        g = F.fks_build_graph_create(F.FKS_KEY_U64, keys, None, None, b.seg_offs, vals)
+        gms = _timed(torch, stream, lambda: F.fks_build_graph_run(g, b.seeds), reps=5)
+        st = F.fks_build_graph_run(g, b.seeds)
+        S = g.mapset()
+        ok = bool((st == 0).all())
+        for j in (0, m // 2, m - 1):  # the graph's tables equal a per-call build's
+            k0, k1 = int(b.seg_offs[j]), int(b.seg_offs[j + 1])
+            pm = F.fks_build_u64(keys[k0:k1], vals[k0:k1], int(b.seeds[j]))
+            d1, s1, _ = F.fks_map_export(S.get(j))
+            d2, s2, _ = F.fks_map_export(pm)
+            ok = ok and np.array_equal(d1, d2) and np.array_equal(s1, s2)
+        r = {"maps": m, "keys": total, "batched_ms": bms, "graph_ms": gms,
+             "graph_kernels": g.kernels(), "graph_speedup": bms / gms,
+             "graph_keys_per_s": total / (gms / 1e3), "tables_match_per_call": ok}
+        if per_call:
+            segs = [(int(b.seg_offs[j]), int(b.seg_offs[j + 1]), int(b.seeds[j])) for j in range(m)]
+
+            def loop():
+                for k0, k1, sd in segs:
+                    F.fks_build_u64(keys[k0:k1], vals[k0:k1], sd)
+            pms = _timed(torch, stream, loop, reps=3)
+            r["per_call_ms"] = pms
+            r["graph_speedup_over_per_call"] = pms / gms
+        del S
+        g.close()
+        res[name] = r
+        torch.cuda.empty_cache()
+    return res
 
 
 def run_bucket_variants(F, torch, hbm, keys, vals, queries, out, found, w, n, nq):
@@ -358,11 +405,11 @@ def run_bucket_variants(F, torch, hbm, keys, vals, queries, out, found, w, n, nq
     return res
 
 
-def run_from_array(F, W, torch, hbm):
+def run_from_array(F, W, torch, hbm, shift=0):
     """from_array (opts.dedup = 1): 2^26 pairs whose keys are drawn with
     replacement from 2^25 distinct keys (about 2.9e7 distinct); the first
     occurrence wins.  Timed: the deduplicating pre-pass + the build."""
-    u, universe = 1 << 26, 1 << 25
+    u, universe = 1 << (26 - shift), 1 << (25 - shift)
     rng = np.random.default_rng(17)
     base = W.key_stream(17, universe)
     keys_h = base[rng.integers(0, universe, u)]
@@ -387,7 +434,8 @@ def run_from_array(F, W, torch, hbm):
     dd = (8 + 32) + (8 + 32 + 4) + 8 + (8 + 16 + 16)
     del m
     torch.cuda.empty_cache()
-    return {"workload": "2^26 u64 pairs, keys drawn from 2^25 distinct, first occurrence wins",
+    return {"workload": "2^%d u64 pairs, keys drawn from 2^%d distinct, first occurrence wins" % (26 - shift,
+                                                                                               25 - shift),
             "distinct_keys": int(info.n), "dedup_plus_build_ms": ms,
             "input_pairs_per_s": u / (ms / 1e3), "prepass_bytes_model": f"{dd} B/pair",
             "first_occurrence_sample_ok": bool(ok)}
@@ -473,6 +521,10 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--serve-rho", type=float, default=0.8)
     ap.add_argument("--n", type=int, default=N_KEYS)
+    ap.add_argument("--no-autotune", action="store_true")
+    # the string, batched, graph and from_array rows at 2^-shift of their
+    # sizes (small cases for profiler captures); 0 = the configured sizes
+    ap.add_argument("--extras-shift", type=int, default=0)
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -498,6 +550,14 @@ def main():
     out = torch.empty(nq, dtype=torch.int64, device="cuda")
     found = torch.empty(nq, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
+    # launch shapes of the build and the lookup, measured on this workload's
+    # size before anything is timed (the timed step then runs at them)
+    tune = None
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        entry, trials = F.fks_autotune(F.FKS_KEY_U64, 1, n=n, nq=nq, seed=rank_seed(rank) + 1)
+        tune = {"seconds": time.perf_counter() - t0, "entry": entry.as_dict(),
+                "trials": [[p, v, round(ms, 4)] for p, v, ms in trials]}
     F.fks_profile_enable(True)
 
     build_ms, part_ms, lookup_ms, step_ms, nonempty, S = [], [], [], [], [], []
@@ -644,6 +704,7 @@ def main():
                 "d2h_bytes_per_step": int(8 * nq + nq), "ms_per_step": e2e_ms},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
+        "autotune": tune,
     }
     # ---- reference point: the search-based map (sort + binary search) on the same data
     if not args.no_search_baseline:
@@ -688,9 +749,11 @@ def main():
     # ---- the other rows of the path: string keys (config 3), batched maps (config 4)
     if not args.no_extras:
         line["bucket_variants"] = run_bucket_variants(F, torch, hbm, keys, vals, queries, out, found, w, n, nq)
-        line["strings"] = run_strings(F, W, torch, hbm)
-        line["batched"] = run_batched(F, W, torch, hbm)
-        line["from_array"] = run_from_array(F, W, torch, hbm)
+        xs = args.extras_shift
+        line["strings"] = run_strings(F, W, torch, hbm, xs)
+        line["batched"] = run_batched(F, W, torch, hbm, xs)
+        line["graph_builds"] = run_graph_builds(F, W, torch, xs)
+        line["from_array"] = run_from_array(F, W, torch, hbm, xs)
     # ---- serving stream (config 5): continuous batching against per-call launches
     if args.serve_requests > 0:
         line["serving"] = run_serving(args, F, W, torch)

@@ -292,8 +292,9 @@ void fks_build_graph_destroy(fks_build_graph_t g);
  *                          levels instead of one (10..40)
  *   lookup_queries_per_thread, lookup_block, lookup_blocks_per_sm
  *                          needles in flight per thread (2, 4, 8), threads
- *                          per block (128, 256, 512) and the grid in blocks
- *                          per SM (1..64) of fks_lookup_u64
+ *                          per block (128, 256, 512) and the grid cap in
+ *                          blocks per SM (1..1024; a grid-stride loop covers
+ *                          what the cap leaves) of fks_lookup_u64
  * A process-wide table holds one entry per (key_kind, keys_per_bucket);
  * builds and uint64 lookups of maps with that lambda use it, else the
  * defaults (3 or 1, 0, 8, 20, 4, 256, 8). */

@@ -109,7 +109,7 @@ bool valid(const fks_tuning& t) {
          (t.lookup_queries_per_thread == 2 || t.lookup_queries_per_thread == 4 ||
           t.lookup_queries_per_thread == 8) &&
          (t.lookup_block == 128 || t.lookup_block == 256 || t.lookup_block == 512) && t.lookup_blocks_per_sm >= 1 &&
-         t.lookup_blocks_per_sm <= 64;
+         t.lookup_blocks_per_sm <= 1024;
 }
 
 void store(const fks_tuning& t) {
@@ -402,7 +402,7 @@ fks_status fks_autotune(fks_key_kind kind, uint32_t keys_per_bucket, uint64_t n,
           lbest = c;
         }
       }
-    for (uint32_t per : {4u, 8u, 16u, 32u}) {
+    for (uint32_t per : {4u, 8u, 32u, 128u, 1024u}) {
       if (result != FKS_OK) break;
       LookupShape c = lbest;
       c.blocks_per_sm = per;

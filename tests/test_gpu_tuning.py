@@ -98,8 +98,8 @@ def test_autotune_u64_then_build_bit_exact(F):
     assert t.tuned == 1 and t.sample_keys == 1 << 20 and t.build_ms > 0 and t.lookup_ms > 0
     assert t.thread_search_max in (1, 2, 3) and t.part_ctas_per_sm in (0, 1, 2)
     assert t.lookup_queries_per_thread in (2, 4, 8) and t.lookup_block in (128, 256, 512)
-    assert t.lookup_blocks_per_sm in (4, 8, 16, 32)
-    assert len(rows) >= 3 + 2 + 2 + 9 + 4 - 1 and all(ms > 0 for _, _, ms in rows)
+    assert t.lookup_blocks_per_sm in (4, 8, 32, 128, 1024)
+    assert len(rows) >= 3 + 2 + 2 + 9 + 5 and all(ms > 0 for _, _, ms in rows)
     got = F.fks_tuning_get(F.FKS_KEY_U64, 1)
     assert got.as_dict() == t.as_dict()
     # builds and lookups now run at the tuned shape, with the same results

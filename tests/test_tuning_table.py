@@ -41,6 +41,7 @@ def test_install_and_reset(F):
                                          ("part_ctas_per_sm", 3), ("scatter_blocks_per_sm", 0),
                                          ("split_min_keys_log2", 9), ("lookup_queries_per_thread", 3),
                                          ("lookup_block", 1024), ("lookup_blocks_per_sm", 0),
+                                         ("lookup_blocks_per_sm", 1025),
                                          ("keys_per_bucket", 3), ("key_kind", 2)])
 def test_out_of_range_entries_are_rejected(F, field, value):
     t = F.fks_tuning_get(F.FKS_KEY_U64, 1)
