@@ -522,6 +522,9 @@ def main():
     ap.add_argument("--serve-rho", type=float, default=0.8)
     ap.add_argument("--n", type=int, default=N_KEYS)
     ap.add_argument("--no-autotune", action="store_true")
+    # install these launch-shape fields (uint64 keys, one bucket per key)
+    # instead of running the autotuner, e.g. lookup_block=512,lookup_blocks_per_sm=1024
+    ap.add_argument("--tuning", default="")
     # the string, batched, graph and from_array rows at 2^-shift of their
     # sizes (small cases for profiler captures); 0 = the configured sizes
     ap.add_argument("--extras-shift", type=int, default=0)
@@ -553,7 +556,14 @@ def main():
     # launch shapes of the build and the lookup, measured on this workload's
     # size before anything is timed (the timed step then runs at them)
     tune = None
-    if not args.no_autotune:
+    if args.tuning:
+        entry = F.fks_tuning_get(F.FKS_KEY_U64, 1)
+        for kv in args.tuning.split(","):
+            k, v = kv.split("=")
+            setattr(entry, k.strip(), int(v))
+        F.fks_tuning_set(entry)
+        tune = {"installed": entry.as_dict()}
+    elif not args.no_autotune:
         t0 = time.perf_counter()
         entry, trials = F.fks_autotune(F.FKS_KEY_U64, 1, n=n, nq=nq, seed=rank_seed(rank) + 1)
         tune = {"seconds": time.perf_counter() - t0, "entry": entry.as_dict(),
