@@ -235,12 +235,23 @@ __global__ void __launch_bounds__(1024) k_scan_parts(PassDev p) {
 // a segment of 2^cls lanes (s <= 32), 6 = the whole CTA.
 constexpr uint32_t kClasses = 7;
 // With at most kCap keys a class of buckets of >= s_min keys has at most
-// kCap / s_min entries: fixed list regions in the work array.
-__host__ __device__ constexpr uint32_t class_region(uint32_t c) {
-  return c == 0 ? 0u : c == 1 ? 1024u : c == 2 ? 2048u : c == 3 ? 2730u : c == 4 ? 3139u : c == 5 ? 3366u : 3486u;
+// kCap / s_min entries (s_min = 2, 2, 3, 5, 9, 17, 33 for classes 0..6; class
+// 1 holds buckets of 2 keys only when one-thread searches stop at a single
+// key): fixed list regions in the work array, a select chain over
+// compile-time constants (the index is a runtime value in the kernel).
+constexpr uint32_t kRegion1 = kCap / 2, kRegion2 = kRegion1 + kCap / 2, kRegion3 = kRegion2 + kCap / 3,
+                   kRegion4 = kRegion3 + kCap / 5, kRegion5 = kRegion4 + kCap / 9,
+                   kRegion6 = kRegion5 + kCap / 17, kWorkEntries = kRegion6 + kCap / 33;
+__host__ __device__ __forceinline__ constexpr uint32_t class_region(uint32_t c) {
+  return c == 0 ? 0u
+         : c == 1 ? kRegion1
+         : c == 2 ? kRegion2
+         : c == 3 ? kRegion3
+         : c == 4 ? kRegion4
+         : c == 5 ? kRegion5
+         : kRegion6;
 }
-constexpr uint32_t kWorkEntries = 3548;  // class_region(6) + kCap / 33
-static_assert(kCap == 2048, "class regions assume 2048 keys per partition");
+static_assert(kCap != 2048 || kWorkEntries == 3548, "class regions of a 2048-key partition");
 
 __host__ __device__ constexpr uint32_t align16(uint32_t x) { return (x + 15u) & ~15u; }
 

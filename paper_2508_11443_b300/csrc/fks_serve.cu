@@ -385,8 +385,10 @@ void scheduler_main(fks_server* S) {
       std::unique_lock<std::mutex> lk(S->mu);
       const bool busy = !S->inflight.empty();
       auto have_work = [&] { return S->stop.load() || !S->arrivals.empty() || !S->build_results.empty(); };
-      if (busy) S->cv.wait_for(lk, std::chrono::microseconds(20), have_work);
-      else S->cv.wait(lk, have_work);
+      // With batches in flight the loop polls their events without sleeping
+      // (a timed wait would add the kernel's timer slack, tens of
+      // microseconds, to every completion); idle, it sleeps until work arrives.
+      if (!busy) S->cv.wait(lk, have_work);
       arrivals.assign(S->arrivals.begin(), S->arrivals.end());
       S->arrivals.clear();
       results.assign(S->build_results.begin(), S->build_results.end());
@@ -399,8 +401,11 @@ void scheduler_main(fks_server* S) {
     }
     for (Req* q : results) apply_build_result(S, q);
     for (Req* q : arrivals) apply_arrival(S, q);
+    const size_t before = S->inflight.size();
     poll_batches(S);
     launch_batches(S);
+    if (arrivals.empty() && results.empty() && S->inflight.size() == before && !S->inflight.empty())
+      std::this_thread::yield();  // nothing changed: let other threads run before the next poll
   }
 }
 
