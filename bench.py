@@ -374,15 +374,18 @@ def run_graph_builds(F, W, torch, shift=0):
     return res
 
 
-def run_bucket_variants(F, torch, hbm, keys, vals, queries, out, found, w, n, nq):
+def run_bucket_variants(F, torch, hbm, keys, vals, queries, out, found, w, n, nq, tune=True):
     """The level-one bucket-count variant on the headline workload: nb =
     ceil(n / lambda) buckets for lambda in 1, 2, 4, 8, 16 (1 is the paper's
     construction).  Fewer buckets keep the descriptor array (8 nb bytes) in
     L2, so lookups approach one DRAM access per query; the slot array grows
-    to about (1 + lambda) n slots."""
+    to about (1 + lambda) n slots.  Each lambda runs at the launch shapes the
+    autotuner measured for it on this size (tune=False: the current table)."""
     stream = torch.cuda.current_stream()
     res = {}
     for lam in (1, 2, 4, 8, 16):
+        if tune and lam > 1:
+            F.fks_autotune(F.FKS_KEY_U64, lam, n=n, nq=nq, seed=SEED + lam)
         o = F.make_opts(keys_per_bucket=lam)
         bms = _timed(torch, stream, lambda: F.fks_build_u64(keys, vals, SEED, o))
         m = F.fks_build_u64(keys, vals, SEED, o)
@@ -399,7 +402,10 @@ def run_bucket_variants(F, torch, hbm, keys, vals, queries, out, found, w, n, nq
             "build_keys_per_s": n / (bms / 1e3), "lookups_per_s": nq / (lms / 1e3),
             "keys_plus_lookups_per_s": (n + nq) / ((bms + lms) / 1e3),
             "lookup_bytes_model": f"{lq:.2f} B/query", "lookup_GBps": lq * nq / (lms / 1e3) / 1e9,
-            "lookup_frac": lq * nq / (lms / 1e3) / 1e9 / hbm, "results_match_truth": bool(ok)}
+            "lookup_frac": lq * nq / (lms / 1e3) / 1e9 / hbm, "results_match_truth": bool(ok),
+            "shape": {k: v for k, v in F.fks_tuning_get(F.FKS_KEY_U64, lam).as_dict().items()
+                      if k in ("thread_search_max", "split_min_keys_log2", "lookup_queries_per_thread",
+                               "lookup_block", "lookup_blocks_per_sm", "tuned")}}
         del m
         torch.cuda.empty_cache()
     return res
@@ -758,7 +764,8 @@ def main():
                           "fks_speedup_build": med(eb) / med(build_ms), "fks_speedup_lookup": med(el) / lk}}
     # ---- the other rows of the path: string keys (config 3), batched maps (config 4)
     if not args.no_extras:
-        line["bucket_variants"] = run_bucket_variants(F, torch, hbm, keys, vals, queries, out, found, w, n, nq)
+        line["bucket_variants"] = run_bucket_variants(F, torch, hbm, keys, vals, queries, out, found, w, n, nq,
+                                                      tune=not (args.no_autotune or args.tuning))
         xs = args.extras_shift
         line["strings"] = run_strings(F, W, torch, hbm, xs)
         line["batched"] = run_batched(F, W, torch, hbm, xs)
