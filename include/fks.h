@@ -343,6 +343,13 @@ fks_status fks_tuning_get(fks_key_kind kind, uint32_t keys_per_bucket, fks_tunin
 fks_status fks_tuning_set(const fks_tuning* h_in);
 /* forget every entry: back to the defaults */
 void fks_tuning_reset(void);
+/* the table to / from a text file (one line per entry), so that a service
+ * tunes once per GPU type and later processes start from the result.  A
+ * malformed or out-of-range line makes fks_tuning_load return
+ * FKS_ERR_INVALID_ARG and install nothing; loaded entries replace the
+ * table's entries for the same (key_kind, keys_per_bucket). */
+fks_status fks_tuning_save(const char* path);
+fks_status fks_tuning_load(const char* path);
 
 /* ------------------------------------------------------------------ no allocation
  * fks_build_u64_noalloc -- the same build as fks_build_u64, for callers that
@@ -524,6 +531,24 @@ fks_status fks_map_info(fks_map_t map, fks_map_info_t* h_out);
  * Any pointer may be NULL. */
 fks_status fks_map_export(fks_map_t map, uint64_t* h_desc, void* h_slots, uint8_t* h_ctx,
                           fks_stream_t stream);
+
+/* fks_map_import -- a map from tables that fks_map_export wrote (checkpoint /
+ * resume: export, store the buffers and the info anywhere, import in another
+ * process or on another GPU).  Not in the paper, whose maps live only as long
+ * as the program that built them.
+ *   h_info   what fks_map_info returned for the exported map: n, seed, round,
+ *            slots, slot_capacity, buckets, keys_per_bucket, key_kind,
+ *            val_type, context_bytes and the statistics are taken from it
+ *   h_desc   uint64[buckets], h_slots (slots of 16 or 32 bytes), h_ctx
+ *            uint8[context_bytes] for string maps: host memory, as exported
+ * The descriptors are checked against the metadata before anything is
+ * uploaded (every non-empty bucket's s^2 slots in order inside the slot
+ * array, sum s = n, sum s^2 = slots); a mismatch returns FKS_ERR_INVALID_ARG.
+ * The map answers lookups exactly as the exported one (the level-one and
+ * fingerprint constants are re-derived from seed and round).  Blocks until
+ * the upload is done; the handle is freed by fks_map_destroy. */
+fks_status fks_map_import(const fks_map_info_t* h_info, const uint64_t* h_desc, const void* h_slots,
+                          const uint8_t* h_ctx, const fks_allocator* alloc, fks_stream_t stream, fks_map_t* out);
 
 void fks_map_destroy(fks_map_t map);
 void fks_mapset_destroy(fks_mapset_t set);

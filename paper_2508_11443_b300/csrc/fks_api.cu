@@ -613,6 +613,7 @@ fks_status SetBuild::run(cudaStream_t st, GraphPass* g) {
 
   while (!active.empty() && hard == FKS_OK) {
     const uint32_t ma = uint32_t(active.size());
+    NvtxRange pass_range(first ? "level-one pass" : "level-one pass (redraw)");
     // the first pass of a recorded build is a launch of its graph
     const bool replay = first && g != nullptr;
     uint8_t* up = replay ? g->up : static_cast<uint8_t*>(g_pin_up.get(up_bytes(ma)));
@@ -796,6 +797,7 @@ struct DedupOut {
 };
 
 static fks_status dedup_inputs(const BuildIn& in, const Alloc& A, cudaStream_t st, DedupOut* out) {
+  NvtxRange range("from_array: deduplication");
   const bool str = in.kind == FKS_KEY_BYTES;
   const uint32_t m = in.m;
   const uint64_t u = uint64_t(in.seg[m]);
@@ -872,6 +874,7 @@ static fks_status dedup_inputs(const BuildIn& in, const Alloc& A, cudaStream_t s
 
 static fks_status build_single(const BuildIn& in, const fks_build_opts* opts,
                                const fks_allocator* alloc, cudaStream_t st, fks_map_t* out) {
+  NvtxRange range("fks_build");
   Opts o;
   if (!read_opts(opts, &o)) return fail(FKS_ERR_INVALID_ARG, "bad build options");
   Alloc A(alloc);
@@ -1118,6 +1121,7 @@ static bool absent_fits(const fks_map* m, int64_t absent) {
 
 fks_status fks_lookup_u64(fks_map_t map, const uint64_t* q, uint64_t nq, void* out_vals,
                           uint8_t* out_found, int64_t absent, fks_stream_t stream) {
+  NvtxRange range("fks_lookup_u64");
   if (!map) return fail(FKS_ERR_INVALID_ARG, "fks_lookup_u64: NULL map");
   if (const fks_status bs = settle(map)) return bs;
   if (map->kind != FKS_KEY_U64) return fail(FKS_ERR_INVALID_ARG, "fks_lookup_u64: not a u64 map");
@@ -1131,6 +1135,7 @@ fks_status fks_lookup_u64(fks_map_t map, const uint64_t* q, uint64_t nq, void* o
 fks_status fks_lookup_bytes(fks_map_t map, const uint8_t* qctx, const int64_t* qoffs, uint64_t nq,
                             void* out_vals, uint8_t* out_found, int64_t absent,
                             fks_stream_t stream) {
+  NvtxRange range("fks_lookup_bytes");
   if (!map) return fail(FKS_ERR_INVALID_ARG, "fks_lookup_bytes: NULL map");
   if (const fks_status bs = settle(map)) return bs;
   if (map->kind != FKS_KEY_BYTES) return fail(FKS_ERR_INVALID_ARG, "fks_lookup_bytes: not a string map");
@@ -1147,6 +1152,7 @@ fks_status fks_build_batched(fks_key_kind kind, const uint64_t* keys, const uint
                              uint32_t m, const void* vals, fks_val_type val_type,
                              const fks_build_opts* opts, const fks_allocator* alloc,
                              fks_stream_t stream, fks_mapset_t* out, fks_status* h_status) {
+  NvtxRange range("fks_build_batched");
   if (!out) return fail(FKS_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (!h_seeds) return fail(FKS_ERR_INVALID_ARG, "fks_build_batched: bad arguments");
@@ -1207,6 +1213,7 @@ fks_status fks_lookup_batched(fks_mapset_t set, const uint32_t* map_ids, const u
                               const uint8_t* qctx, const int64_t* qoffs, uint64_t nq,
                               void* out_vals, uint8_t* out_found, int64_t absent,
                               fks_stream_t stream) {
+  NvtxRange range("fks_lookup_batched");
   if (!set) return fail(FKS_ERR_INVALID_ARG, "fks_lookup_batched: set is NULL");
   if (nq == 0) return FKS_OK;
   const bool str = set->kind == FKS_KEY_BYTES;
@@ -1224,6 +1231,7 @@ fks_status fks_build_graph_create(fks_key_kind kind, const uint64_t* keys, const
                                   const int64_t* offs, const int64_t* h_seg, uint32_t m, const void* vals,
                                   fks_val_type val_type, const fks_build_opts* opts, const fks_allocator* alloc,
                                   fks_stream_t stream, fks_build_graph_t* out) {
+  NvtxRange range("fks_build_graph_create");
   if (!out) return fail(FKS_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   std::vector<int64_t> seg;
@@ -1290,6 +1298,7 @@ fks_status fks_build_graph_create(fks_key_kind kind, const uint64_t* keys, const
 
 fks_status fks_build_graph_run(fks_build_graph_t g, const uint64_t* h_seeds, fks_stream_t stream,
                                fks_status* h_status) {
+  NvtxRange range("fks_build_graph_run");
   if (!g || !h_seeds) return fail(FKS_ERR_INVALID_ARG, "fks_build_graph_run: NULL argument");
   std::lock_guard<std::mutex> lock(g->mu);
   const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -1364,6 +1373,83 @@ fks_status fks_map_export(fks_map_t map, uint64_t* h_desc, void* h_slots, uint8_
   if (h_ctx && map->kind == FKS_KEY_BYTES && map->ctx_bytes)
     FKS_CUDA(cudaMemcpyAsync(h_ctx, map->ctx, map->ctx_bytes, cudaMemcpyDeviceToHost, st));
   FKS_CUDA(cudaStreamSynchronize(st));
+  return FKS_OK;
+}
+
+fks_status fks_map_import(const fks_map_info_t* h_info, const uint64_t* h_desc, const void* h_slots,
+                          const uint8_t* h_ctx, const fks_allocator* alloc, fks_stream_t stream, fks_map_t* out) {
+  NvtxRange range("fks_map_import");
+  if (!out) return fail(FKS_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!h_info || !h_desc || !h_slots) return fail(FKS_ERR_INVALID_ARG, "fks_map_import: NULL argument");
+  const fks_map_info_t& I = *h_info;
+  const bool str = I.key_kind == FKS_KEY_BYTES;
+  const uint32_t lam = I.keys_per_bucket ? I.keys_per_bucket : 1u;
+  if ((I.key_kind != FKS_KEY_U64 && !str) || (I.val_type != FKS_VAL_I32 && I.val_type != FKS_VAL_I64) ||
+      I.n == 0 || I.n >= (1ull << 30) || (lam != 1 && lam != 2 && lam != 4 && lam != 8 && lam != 16) ||
+      I.buckets != level1_buckets(I.n, lam) || I.slots == 0 || I.slots > I.slot_capacity ||
+      I.slot_capacity > 0xFFFFFFFFull || (str && (!h_ctx || I.context_bytes >= (1ull << 40))))
+    return fail(FKS_ERR_INVALID_ARG, "fks_map_import: metadata out of range");
+  // the descriptors must describe the slot array: every non-empty bucket's
+  // s^2 slots inside it, sum s = n, sum s^2 = S, and the ranges in order
+  uint64_t keys = 0, next = 0;
+  for (uint64_t b = 0; b < I.buckets; ++b) {
+    const uint64_t d = h_desc[b];
+    const uint64_t s = desc_s(d);
+    if (s == 0) continue;
+    const uint64_t off = desc_off(d);
+    if (off != next || off + s * s > I.slots)
+      return fail(FKS_ERR_INVALID_ARG, "fks_map_import: descriptors do not match the slot array");
+    next = off + s * s;
+    keys += s;
+  }
+  if (keys != I.n || next != I.slots)
+    return fail(FKS_ERR_INVALID_ARG, "fks_map_import: descriptors do not match n or the slot count");
+  const int W = str ? 4 : 2;
+  Alloc A(alloc);
+  const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  Carve cm;
+  const size_t o_desc = cm.take<uint64_t>(I.buckets);
+  const size_t o_slots = cm.take<uint64_t>(I.slots * W);
+  const size_t o_ctx = cm.take<uint8_t>(str ? I.context_bytes + 16 : 0);
+  uint8_t* block = static_cast<uint8_t*>(A.get(cm.off, st));
+  if (!block) return fail(FKS_ERR_OUT_OF_MEMORY, "fks_map_import: allocation");
+  cudaError_t e = cudaMemcpyAsync(block + o_desc, h_desc, sizeof(uint64_t) * I.buckets, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(block + o_slots, h_slots, sizeof(uint64_t) * W * I.slots, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && str && I.context_bytes)
+    e = cudaMemcpyAsync(block + o_ctx, h_ctx, I.context_bytes, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    A.put(block, cm.off, st);
+    return cuda_fail(e, "fks_map_import: upload");
+  }
+  fks_map* m = new fks_map();
+  m->kind = fks_key_kind(I.key_kind);
+  m->vt = fks_val_type(I.val_type);
+  m->n = I.n;
+  m->seed = I.seed;
+  m->round = I.round;
+  m->c1 = derive(I.seed, I.round, kTagLevel1, 0);
+  m->fpb = fp_base(I.seed, I.round);
+  m->S = I.slots;
+  m->slot_cap = I.slot_capacity;
+  m->att_sum = I.attempts_sum;
+  m->max_s = I.max_bucket;
+  m->max_att = I.max_attempt;
+  m->overflow = I.overflow_partitions;
+  m->nonempty = I.nonempty_buckets;
+  m->nb = I.buckets;
+  m->lambda = lam;
+  m->desc = reinterpret_cast<uint64_t*>(block + o_desc);
+  m->slots = reinterpret_cast<uint64_t*>(block + o_slots);
+  m->ctx = str ? block + o_ctx : nullptr;
+  m->ctx_bytes = str ? I.context_bytes : 0;
+  m->block = block;
+  m->block_bytes = cm.off;
+  m->alloc = A;
+  m->bytes = cm.off;
+  *out = m;
   return FKS_OK;
 }
 

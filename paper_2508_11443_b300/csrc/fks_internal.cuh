@@ -2,6 +2,7 @@
 // of the library (not part of the public ABI).
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "fks_device.cuh"
@@ -112,6 +113,15 @@ struct PassDev {
   uint64_t* desc;             // descriptor array of the set
   uint64_t* slots;            // slot array of the set (2 or 4 words per slot)
   BuildCfg cfg;
+};
+
+// An NVTX range for the lifetime of the object (host code): the entry points
+// and the phases of a build show up by name in a profiler's timeline.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
 // Process-wide count of kernels launched by the library (fks_api.cu).

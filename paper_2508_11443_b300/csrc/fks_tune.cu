@@ -27,6 +27,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <stdio.h>
+
 #include <algorithm>
 #include <chrono>
 #include <mutex>
@@ -227,9 +229,64 @@ void fks_tuning_reset(void) {
   g_table.clear();
 }
 
+// One line per entry: a tag, the version, then the fields in declaration order.
+fks_status fks_tuning_save(const char* path) {
+  if (!path) return FKS_ERR_INVALID_ARG;
+  std::vector<fks_tuning> copy;
+  {
+    std::lock_guard<std::mutex> lock(g_mu);
+    copy = g_table;
+  }
+  FILE* f = fopen(path, "w");
+  if (!f) return FKS_ERR_INVALID_ARG;
+  for (const fks_tuning& t : copy)
+    fprintf(f, "fks_tuning 1 %u %u %u %u %u %u %u %u %u %u %.6g %.6g %llu\n", t.key_kind, t.keys_per_bucket,
+            t.thread_search_max, t.part_ctas_per_sm, t.scatter_blocks_per_sm, t.split_min_keys_log2,
+            t.lookup_queries_per_thread, t.lookup_block, t.lookup_blocks_per_sm, t.tuned, double(t.build_ms),
+            double(t.lookup_ms), static_cast<unsigned long long>(t.sample_keys));
+  const bool ok = fflush(f) == 0;
+  fclose(f);
+  return ok ? FKS_OK : FKS_ERR_INVALID_ARG;
+}
+
+fks_status fks_tuning_load(const char* path) {
+  if (!path) return FKS_ERR_INVALID_ARG;
+  FILE* f = fopen(path, "r");
+  if (!f) return FKS_ERR_INVALID_ARG;
+  std::vector<fks_tuning> entries;
+  char line[512];
+  bool bad = false;
+  while (fgets(line, sizeof(line), f)) {
+    if (line[0] == '\n' || line[0] == '#') continue;
+    fks_tuning t;
+    memset(&t, 0, sizeof(t));
+    t.struct_size = sizeof(fks_tuning);
+    unsigned version = 0;
+    double bms = 0, lms = 0;
+    unsigned long long nk = 0;
+    const int got = sscanf(line, "fks_tuning %u %u %u %u %u %u %u %u %u %u %u %lg %lg %llu", &version, &t.key_kind,
+                           &t.keys_per_bucket, &t.thread_search_max, &t.part_ctas_per_sm, &t.scatter_blocks_per_sm,
+                           &t.split_min_keys_log2, &t.lookup_queries_per_thread, &t.lookup_block,
+                           &t.lookup_blocks_per_sm, &t.tuned, &bms, &lms, &nk);
+    t.build_ms = float(bms);
+    t.lookup_ms = float(lms);
+    t.sample_keys = nk;
+    if (got != 14 || version != 1 || !valid(t)) {
+      bad = true;
+      break;
+    }
+    entries.push_back(t);
+  }
+  fclose(f);
+  if (bad) return FKS_ERR_INVALID_ARG;  // nothing installed from a malformed file
+  for (const fks_tuning& t : entries) store(t);
+  return FKS_OK;
+}
+
 fks_status fks_autotune(fks_key_kind kind, uint32_t keys_per_bucket, uint64_t n, uint64_t nq, uint64_t seed,
                         fks_stream_t stream, fks_tuning* h_out, fks_tune_trial* h_trials, uint32_t max_trials,
                         uint32_t* h_count) {
+  NvtxRange range("fks_autotune");
   if (h_count) *h_count = 0;
   if ((kind != FKS_KEY_U64 && kind != FKS_KEY_BYTES) || !valid_lambda(keys_per_bucket)) return FKS_ERR_INVALID_ARG;
   if (n == 0) n = 1ull << 22;

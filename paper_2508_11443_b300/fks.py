@@ -451,6 +451,24 @@ def fks_tuning_reset():
     _tune_lib().fks_tuning_reset()
 
 
+def fks_tuning_save(path: str):
+    L = _tune_lib()
+    L.fks_tuning_save.argtypes = [ctypes.c_char_p]
+    L.fks_tuning_save.restype = ctypes.c_int
+    st = L.fks_tuning_save(path.encode())
+    if st != FKS_OK:
+        raise FksError(st, f"could not write {path}")
+
+
+def fks_tuning_load(path: str):
+    L = _tune_lib()
+    L.fks_tuning_load.argtypes = [ctypes.c_char_p]
+    L.fks_tuning_load.restype = ctypes.c_int
+    st = L.fks_tuning_load(path.encode())
+    if st != FKS_OK:
+        raise FksError(st, f"could not read a tuning table from {path}")
+
+
 def fks_build_u64_noalloc(keys, vals, seed: int, desc_out, slots_out,
                           opts: fks_build_opts | None = None, stream=None) -> fks_map_info_t:
     """The allocation-free build: the caller owns every output buffer
@@ -490,6 +508,42 @@ def fks_map_export(m: Map, stream=None):
     if ctx is not None:
         ctx = ctx[: info.context_bytes]
     return desc, slots, ctx
+
+
+def fks_map_import(info: fks_map_info_t, desc: np.ndarray, slots: np.ndarray, ctx=None, stream=None) -> Map:
+    """A map from exported tables (host arrays as fks_map_export returns them)."""
+    L = lib()
+    L.fks_map_import.argtypes = [ctypes.POINTER(fks_map_info_t), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                 ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+    L.fks_map_import.restype = ctypes.c_int
+    desc = np.ascontiguousarray(desc, np.uint64)
+    slots = np.ascontiguousarray(slots, np.uint64)
+    cptr = None
+    if ctx is not None:
+        ctx = np.ascontiguousarray(ctx, np.uint8)
+        cptr = ctx.ctypes.data_as(ctypes.c_void_p) if ctx.size else ctypes.c_void_p(np.zeros(1, np.uint8).ctypes.data)
+    h = ctypes.c_void_p()
+    _check(L.fks_map_import(ctypes.byref(info), desc.ctypes.data_as(ctypes.c_void_p),
+                            slots.ctypes.data_as(ctypes.c_void_p), cptr, None, _stream(stream), ctypes.byref(h)))
+    return Map(h.value)
+
+
+def fks_map_save(m: Map, path: str, stream=None):
+    """Checkpoint a map: its tables and metadata into one .npz file."""
+    info = fks_map_info(m)
+    desc, slots, ctx = fks_map_export(m, stream)
+    meta = np.array([getattr(info, k) for k, _ in fks_map_info_t._fields_], np.uint64)
+    np.savez(path, meta=meta, desc=desc, slots=slots, ctx=ctx if ctx is not None else np.zeros(0, np.uint8))
+
+
+def fks_map_load(path: str, stream=None) -> Map:
+    """Resume a map saved by fks_map_save."""
+    z = np.load(path)
+    info = fks_map_info_t()
+    for (k, _), v in zip(fks_map_info_t._fields_, z["meta"].tolist()):
+        setattr(info, k, int(v))
+    ctx = z["ctx"] if info.key_kind == FKS_KEY_BYTES else None
+    return fks_map_import(info, z["desc"], z["slots"], ctx, stream)
 
 
 class SortMap:

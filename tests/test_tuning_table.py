@@ -54,3 +54,35 @@ def test_out_of_range_entries_are_rejected(F, field, value):
 def test_bad_keys_per_bucket_is_rejected(F):
     with pytest.raises(F.FksError):
         F.fks_tuning_get(F.FKS_KEY_U64, 3)
+
+
+def test_save_and_load_round_trip(F, tmp_path):
+    F.fks_tuning_reset()
+    a = F.fks_tuning_get(F.FKS_KEY_U64, 1)
+    a.lookup_block, a.lookup_blocks_per_sm, a.tuned, a.build_ms, a.sample_keys = 512, 1024, 1, 3.98, 1 << 26
+    F.fks_tuning_set(a)
+    b = F.fks_tuning_get(F.FKS_KEY_BYTES, 16)
+    b.thread_search_max, b.split_min_keys_log2 = 2, 22
+    F.fks_tuning_set(b)
+    path = str(tmp_path / "tune.txt")
+    F.fks_tuning_save(path)
+    F.fks_tuning_reset()
+    assert F.fks_tuning_get(F.FKS_KEY_U64, 1).lookup_block == 256
+    F.fks_tuning_load(path)
+    got_a, got_b = F.fks_tuning_get(F.FKS_KEY_U64, 1), F.fks_tuning_get(F.FKS_KEY_BYTES, 16)
+    assert (got_a.lookup_block, got_a.lookup_blocks_per_sm, got_a.tuned, got_a.sample_keys) == (512, 1024, 1, 1 << 26)
+    assert abs(got_a.build_ms - 3.98) < 1e-4
+    assert (got_b.thread_search_max, got_b.split_min_keys_log2) == (2, 22)
+    F.fks_tuning_reset()
+
+
+def test_malformed_tuning_file_installs_nothing(F, tmp_path):
+    F.fks_tuning_reset()
+    path = tmp_path / "bad.txt"
+    path.write_text("fks_tuning 1 0 1 2 0 8 20 4 512 8 1 1.0 1.0 100\n"
+                    "fks_tuning 1 0 4 9 0 8 20 4 256 8 1 1.0 1.0 100\n")  # thread_search_max 9: out of range
+    with pytest.raises(F.FksError):
+        F.fks_tuning_load(str(path))
+    assert F.fks_tuning_get(F.FKS_KEY_U64, 1).thread_search_max == 3  # the good first line was not installed
+    with pytest.raises(F.FksError):
+        F.fks_tuning_load(str(tmp_path / "missing.txt"))
