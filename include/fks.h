@@ -290,6 +290,10 @@ void fks_build_graph_destroy(fks_build_graph_t g);
  *   scatter_blocks_per_sm  blocks per SM of the one-level count / scatter (1..64)
  *   split_min_keys_log2    passes of >= 2^x keys are grouped in two radix
  *                          levels instead of one (10..40)
+ *   part_prefetch          1: a partition CTA takes its next partition and
+ *                          stages its keys while it searches the current one;
+ *                          0: only once it is free (shorter look-back waits
+ *                          for partitions that write their slots directly)
  *   lookup_queries_per_thread, lookup_block, lookup_blocks_per_sm
  *                          needles in flight per thread (2, 4, 8), threads
  *                          per block (128, 256, 512) and the grid cap in
@@ -297,7 +301,8 @@ void fks_build_graph_destroy(fks_build_graph_t g);
  *                          what the cap leaves) of fks_lookup_u64
  * A process-wide table holds one entry per (key_kind, keys_per_bucket);
  * builds and uint64 lookups of maps with that lambda use it, else the
- * defaults (3 or 1, 0, 8, 20, 4, 256, 8). */
+ * defaults (thread_search_max 3, or 1 for lambda >= 8; 0; 8; 20;
+ * part_prefetch 1, or 0 for lambda 16; 4; 256; 8). */
 typedef struct {
   size_t struct_size;           /* sizeof(fks_tuning)                            */
   uint32_t key_kind;            /* fks_key_kind of the entry                     */
@@ -313,11 +318,14 @@ typedef struct {
   float build_ms;               /* the sample build at the chosen shape          */
   float lookup_ms;              /* the sample lookup at the chosen shape         */
   uint64_t sample_keys;         /* keys of the sample it was measured on         */
+  uint32_t part_prefetch;
+  uint32_t reserved;
 } fks_tuning;
 
 /* One measured candidate: param 0 thread_search_max, 1 part_ctas_per_sm,
  * 2 scatter_blocks_per_sm, 3 split_min_keys_log2, 4 lookup_queries_per_thread
- * << 16 | lookup_block, 5 lookup_blocks_per_sm; ms is the median time. */
+ * << 16 | lookup_block, 5 lookup_blocks_per_sm, 6 part_prefetch; ms is the
+ * median time. */
 typedef struct {
   uint32_t param;
   uint32_t value;

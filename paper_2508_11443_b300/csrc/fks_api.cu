@@ -511,6 +511,7 @@ fks_status SetBuild::init(const BuildIn& in_, const Opts& o_, const Alloc& A_, c
   p.cfg.spin_limit = o.spin;
   p.cfg.hold_first = uint32_t(g_hold_first_partition);
   p.cfg.thread_max = bs.thread_max;
+  p.cfg.prefetch = bs.prefetch;
   return FKS_OK;
 }
 

@@ -953,6 +953,17 @@ __global__ void __launch_bounds__(kPartThreads, PW == 1 ? 2 : 1) k_part_build(Pa
   __syncthreads();
   uint32_t last_j = 0xFFFFFFFFu;  // thread 32: the map held in sM[(iter & 1) ^ 1]
   for (;;) {
+    if (!p.cfg.prefetch && iter > 0) {
+      // Without prefetch the next ticket is taken only when the CTA is free:
+      // a partition is then never queued behind another partition's search,
+      // so the predecessors whose aggregates its look-back needs are already
+      // running (what partitions that write their slots directly wait for).
+      if (t == 0 && !ctl.abort) {
+        ctl.next_gp = atomicAdd(p.ticket, 1u);
+        ctl.next_issued = issue_stage<PW>(p, ctl.next_gp, raw_key, raw_pay, &bar, &ctl.next_e0, &ctl.next_e1);
+      }
+      __syncthreads();
+    }
     const uint32_t gp = ctl.next_gp;
     const uint32_t issued = ctl.next_issued;
     if (gp >= p.P || ctl.abort) break;
@@ -1039,7 +1050,7 @@ __global__ void __launch_bounds__(kPartThreads, PW == 1 ? 2 : 1) k_part_build(Pa
     // raw* is free again: stage the next partition while this one is searched
     // (by the last warp, which rarely has search work: the worklist fills
     // the low warps first)
-    if (t == kPartThreads - 32) {
+    if (p.cfg.prefetch && t == kPartThreads - 32) {
       ctl.next_gp = atomicAdd(p.ticket, 1u);
       ctl.next_issued = issue_stage<PW>(p, ctl.next_gp, raw_key, raw_pay, &bar, &ctl.next_e0, &ctl.next_e1);
     }

@@ -78,6 +78,7 @@ struct BuildCfg {
   uint32_t spin_limit;   // polls of a look-back wait before giving up
   uint32_t hold_first;   // test hook: partition 0 never publishes (forces a timeout)
   uint32_t thread_max;   // buckets of 2 .. thread_max keys are searched by one thread each
+  uint32_t prefetch;     // 1: take the next partition's ticket and stage its keys during the search
 };
 
 // Everything a pass's kernels read; passed by value.
@@ -136,6 +137,7 @@ struct BuildShape {
   uint32_t part_ctas_per_sm;       // partition-build CTAs per SM (capped by occupancy)
   uint32_t scatter_blocks_per_sm;  // grid of the one-level count / scatter kernels
   uint32_t split_min_log2;         // passes of >= 2^x keys are grouped in two radix levels
+  uint32_t prefetch;               // 1: a partition CTA takes its next ticket during the search
 };
 struct LookupShape {
   uint32_t queries_per_thread;  // 2, 4 or 8 needles in flight per thread

@@ -176,6 +176,7 @@ extern "C" fks_status fks_build_u64_noalloc(const uint64_t* keys, const void* va
   p.cfg.spin_limit = spin;
   p.cfg.hold_first = 0;
   p.cfg.thread_max = 3;
+  p.cfg.prefetch = 1;
 
   // control words live on the host stack (pageable copies; nothing allocated)
   const uint64_t h_pseg[2] = {0, n};

@@ -47,6 +47,11 @@ BuildShape default_build_shape(uint32_t lambda) {
   s.part_ctas_per_sm = 0;  // as many as fit
   s.scatter_blocks_per_sm = 8;
   s.split_min_log2 = 20;
+  // staging the next partition during the search pays up to 8 keys per
+  // bucket (2^26 keys: 4.01 vs 4.14 ms at lambda 1, 6.01 vs 6.15 ms at 8);
+  // with 16, whose partitions need their slot prefix before the search, the
+  // longer look-back behind queued partitions costs more (7.29 vs 6.94 ms)
+  s.prefetch = lambda <= 8 ? 1u : 0u;
   return s;
 }
 
@@ -76,6 +81,7 @@ BuildShape build_of(const fks_tuning& t) {
   s.part_ctas_per_sm = t.part_ctas_per_sm;
   s.scatter_blocks_per_sm = t.scatter_blocks_per_sm;
   s.split_min_log2 = t.split_min_keys_log2;
+  s.prefetch = t.part_prefetch;
   return s;
 }
 
@@ -96,6 +102,7 @@ void fill(fks_tuning* t, uint32_t kind, uint32_t lambda, const BuildShape& b, co
   t->part_ctas_per_sm = b.part_ctas_per_sm;
   t->scatter_blocks_per_sm = b.scatter_blocks_per_sm;
   t->split_min_keys_log2 = b.split_min_log2;
+  t->part_prefetch = b.prefetch;
   t->lookup_queries_per_thread = l.queries_per_thread;
   t->lookup_block = l.block;
   t->lookup_blocks_per_sm = l.blocks_per_sm;
@@ -107,7 +114,7 @@ bool valid(const fks_tuning& t) {
   return t.struct_size >= sizeof(fks_tuning) && (t.key_kind == FKS_KEY_U64 || t.key_kind == FKS_KEY_BYTES) &&
          valid_lambda(t.keys_per_bucket) && t.thread_search_max >= 1 && t.thread_search_max <= kThreadSearchMax &&
          t.part_ctas_per_sm <= 2 && t.scatter_blocks_per_sm >= 1 && t.scatter_blocks_per_sm <= 64 &&
-         t.split_min_keys_log2 >= 10 && t.split_min_keys_log2 <= 40 &&
+         t.split_min_keys_log2 >= 10 && t.split_min_keys_log2 <= 40 && t.part_prefetch <= 1 &&
          (t.lookup_queries_per_thread == 2 || t.lookup_queries_per_thread == 4 ||
           t.lookup_queries_per_thread == 8) &&
          (t.lookup_block == 128 || t.lookup_block == 256 || t.lookup_block == 512) && t.lookup_blocks_per_sm >= 1 &&
@@ -240,10 +247,10 @@ fks_status fks_tuning_save(const char* path) {
   FILE* f = fopen(path, "w");
   if (!f) return FKS_ERR_INVALID_ARG;
   for (const fks_tuning& t : copy)
-    fprintf(f, "fks_tuning 1 %u %u %u %u %u %u %u %u %u %u %.6g %.6g %llu\n", t.key_kind, t.keys_per_bucket,
+    fprintf(f, "fks_tuning 2 %u %u %u %u %u %u %u %u %u %u %.6g %.6g %llu %u\n", t.key_kind, t.keys_per_bucket,
             t.thread_search_max, t.part_ctas_per_sm, t.scatter_blocks_per_sm, t.split_min_keys_log2,
             t.lookup_queries_per_thread, t.lookup_block, t.lookup_blocks_per_sm, t.tuned, double(t.build_ms),
-            double(t.lookup_ms), static_cast<unsigned long long>(t.sample_keys));
+            double(t.lookup_ms), static_cast<unsigned long long>(t.sample_keys), t.part_prefetch);
   const bool ok = fflush(f) == 0;
   fclose(f);
   return ok ? FKS_OK : FKS_ERR_INVALID_ARG;
@@ -264,14 +271,17 @@ fks_status fks_tuning_load(const char* path) {
     unsigned version = 0;
     double bms = 0, lms = 0;
     unsigned long long nk = 0;
-    const int got = sscanf(line, "fks_tuning %u %u %u %u %u %u %u %u %u %u %u %lg %lg %llu", &version, &t.key_kind,
+    const int got = sscanf(line, "fks_tuning %u %u %u %u %u %u %u %u %u %u %u %lg %lg %llu %u", &version, &t.key_kind,
                            &t.keys_per_bucket, &t.thread_search_max, &t.part_ctas_per_sm, &t.scatter_blocks_per_sm,
                            &t.split_min_keys_log2, &t.lookup_queries_per_thread, &t.lookup_block,
-                           &t.lookup_blocks_per_sm, &t.tuned, &bms, &lms, &nk);
+                           &t.lookup_blocks_per_sm, &t.tuned, &bms, &lms, &nk, &t.part_prefetch);
     t.build_ms = float(bms);
     t.lookup_ms = float(lms);
     t.sample_keys = nk;
-    if (got != 14 || version != 1 || !valid(t)) {
+    // version 1 lines have no part_prefetch: the default for their lambda
+    if (version == 1 && got == 14) t.part_prefetch = default_build_shape(t.keys_per_bucket).prefetch;
+    const bool complete = (version == 1 && got == 14) || (version == 2 && got == 15);
+    if (!complete || !valid(t)) {
       bad = true;
       break;
     }
@@ -399,6 +409,7 @@ fks_status fks_autotune(fks_key_kind kind, uint32_t keys_per_bucket, uint64_t n,
     }
   };
   sweep(0, {1, 2, 3}, &BuildShape::thread_max);
+  sweep(6, {0, 1}, &BuildShape::prefetch);
   sweep(1, {1, 2}, &BuildShape::part_ctas_per_sm);
   {
     // one or two grouping levels at this size: the threshold goes just below

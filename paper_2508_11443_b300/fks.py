@@ -386,10 +386,11 @@ class fks_tuning(ctypes.Structure):
                 ("split_min_keys_log2", ctypes.c_uint32), ("lookup_queries_per_thread", ctypes.c_uint32),
                 ("lookup_block", ctypes.c_uint32), ("lookup_blocks_per_sm", ctypes.c_uint32),
                 ("tuned", ctypes.c_uint32), ("build_ms", ctypes.c_float), ("lookup_ms", ctypes.c_float),
-                ("sample_keys", ctypes.c_uint64)]
+                ("sample_keys", ctypes.c_uint64), ("part_prefetch", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "struct_size"}
+        return {k: getattr(self, k) for k, _ in self._fields_ if k not in ("struct_size", "reserved")}
 
 
 class fks_tune_trial(ctypes.Structure):
@@ -397,7 +398,7 @@ class fks_tune_trial(ctypes.Structure):
 
 
 TUNE_PARAMS = ("thread_search_max", "part_ctas_per_sm", "scatter_blocks_per_sm", "split_min_keys_log2",
-               "lookup_queries_per_thread<<16|lookup_block", "lookup_blocks_per_sm")
+               "lookup_queries_per_thread<<16|lookup_block", "lookup_blocks_per_sm", "part_prefetch")
 
 
 def _tune_lib():

@@ -29,7 +29,8 @@ def dev(a):
     return torch.from_numpy(a).cuda()
 
 
-SHAPES = [dict(thread_search_max=1), dict(thread_search_max=2), dict(part_ctas_per_sm=1),
+SHAPES = [dict(thread_search_max=1), dict(thread_search_max=2), dict(part_ctas_per_sm=1), dict(part_prefetch=0),
+          dict(part_prefetch=1, thread_search_max=3),
           dict(split_min_keys_log2=16), dict(split_min_keys_log2=30, scatter_blocks_per_sm=3),
           dict(thread_search_max=1, part_ctas_per_sm=1, split_min_keys_log2=12, scatter_blocks_per_sm=32)]
 
@@ -55,7 +56,7 @@ def test_build_shapes_give_the_same_tables(F, shape, lam):
     F.fks_tuning_reset()
 
 
-@pytest.mark.parametrize("shape", [SHAPES[0], SHAPES[3], SHAPES[5]])
+@pytest.mark.parametrize("shape", [SHAPES[0], SHAPES[3], SHAPES[5], SHAPES[7]])
 def test_string_build_shapes_give_the_same_tables(F, shape):
     s = W.string_workload(70000, 100, 0.5, seed=8)
     om = O.build_bytes(s.ctx, s.offs, s.vals, seed=9)
@@ -99,7 +100,8 @@ def test_autotune_u64_then_build_bit_exact(F):
     assert t.thread_search_max in (1, 2, 3) and t.part_ctas_per_sm in (0, 1, 2)
     assert t.lookup_queries_per_thread in (2, 4, 8) and t.lookup_block in (128, 256, 512)
     assert t.lookup_blocks_per_sm in (4, 8, 32, 128, 1024)
-    assert len(rows) >= 3 + 2 + 2 + 9 + 5 and all(ms > 0 for _, _, ms in rows)
+    assert t.part_prefetch in (0, 1)
+    assert len(rows) >= 3 + 2 + 2 + 2 + 9 + 5 and all(ms > 0 for _, _, ms in rows)
     got = F.fks_tuning_get(F.FKS_KEY_U64, 1)
     assert got.as_dict() == t.as_dict()
     # builds and lookups now run at the tuned shape, with the same results
