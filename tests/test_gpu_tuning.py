@@ -129,3 +129,37 @@ def test_autotune_strings(F):
     d, sl, _ = F.fks_map_export(m)
     assert np.array_equal(d, om.desc) and np.array_equal(sl, om.slots)
     F.fks_tuning_reset()
+
+
+@pytest.mark.parametrize("lam,fields", [
+    (1, dict(lookup_queries_per_thread=4, lookup_block=512, lookup_blocks_per_sm=1024)),
+    (16, dict(thread_search_max=2, part_prefetch=0, lookup_queries_per_thread=4, lookup_block=256,
+              lookup_blocks_per_sm=1024))])
+def test_full_size_at_the_benchmark_shapes(F, lam, fields):
+    """2^26 keys and 2^26 queries (90 % hits) at the launch shapes the
+    benchmark's autotuner chose on a B300: every lookup output against the
+    workload's truth, and the tables equal to a build at the default shapes
+    (whose tables the full-size oracle tests pin)."""
+    import torch
+    n = 1 << 26
+    w = W.u64_workload(n, n, 0.9, seed=2)
+    keys, vals, q = dev(w.keys), dev(w.vals), dev(w.queries)
+    o = F.make_opts(keys_per_bucket=lam)
+    F.fks_tuning_reset()
+    ref = F.fks_build_u64(keys, vals, 2, o)
+    d0, s0, _ = F.fks_map_export(ref)
+    del ref
+    install(F, F.FKS_KEY_U64, lam, **fields)
+    m = F.fks_build_u64(keys, vals, 2, o)
+    d1, s1, _ = F.fks_map_export(m)
+    assert np.array_equal(d0, d1) and np.array_equal(s0, s1)
+    del d0, s0, d1, s1
+    out = torch.empty(n, dtype=torch.int64, device="cuda")
+    found = torch.empty(n, dtype=torch.uint8, device="cuda")
+    F.fks_lookup_u64(m, q, out, found, -1)
+    torch.cuda.synchronize()
+    assert np.array_equal(found.cpu().numpy(), w.expect_found)
+    assert np.array_equal(out.cpu().numpy(), np.where(w.expect_found == 1, w.expect_vals, -1))
+    F.fks_tuning_reset()
+    del m, out, found, keys, vals, q
+    torch.cuda.empty_cache()
