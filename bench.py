@@ -491,7 +491,11 @@ def run_serving(args, F, W, torch):
     m = plan.kind.size - pre
     sat = once(F.FKS_SERVE_PER_CALL, np.zeros(m))
     mu = sat["throughput_req_per_s"]
+    # saturation of the batched server on the same stream (every request at once)
+    sat_b = once(F.FKS_SERVE_BATCHED, np.zeros(m))
     out = {"requests": m, "prefill_builds": pre, "budget_gb": 40, "mu_per_call_req_per_s": mu,
+           "mu_batched_req_per_s": sat_b["throughput_req_per_s"],
+           "saturation_throughput_ratio_batched_over_per_call": sat_b["throughput_req_per_s"] / mu,
            "rho": args.serve_rho, "rate_req_per_s": args.serve_rho * mu}
     arrival = W.poisson_arrivals_us(m, args.serve_rho * mu, 5)
     out["per_call"] = once(F.FKS_SERVE_PER_CALL, arrival)
