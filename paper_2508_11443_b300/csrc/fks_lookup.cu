@@ -48,8 +48,8 @@ __device__ __forceinline__ ulonglong2 ld_na_u128(const uint64_t* p, uint64_t pol
 
 // One 32-byte load (a single request, like a 16-byte one): a whole string
 // slot {fingerprint, offset | length << 40, value, 0}.  p is 32-byte aligned.
-__device__ __forceinline__ ulonglong4 ld_na_u256(const uint64_t* p, uint64_t pol) {
-  ulonglong4 v;
+__device__ __forceinline__ ulonglong4_32a ld_na_u256(const uint64_t* p, uint64_t pol) {
+  ulonglong4_32a v;
   asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u64 {%0, %1, %2, %3}, [%4], %5;"
                : "=l"(v.x), "=l"(v.y), "=l"(v.z), "=l"(v.w)
                : "l"(p), "l"(pol));
@@ -150,7 +150,7 @@ __device__ __forceinline__ bool lookup_one_bytes(const LookupMap& M, const uint8
   if (!sz) return false;
   const HashConsts c = derive(M.seed, M.round, b, desc_attempt(d));
   const uint32_t jj = desc_off(d) + reduce32(hash32(c, h), sz * sz);
-  const ulonglong4 w = ld_na_u256(M.slots + 4ull * jj, strm);  // the whole slot, value included
+  const ulonglong4_32a w = ld_na_u256(M.slots + 4ull * jj, strm);  // the whole slot, value included
   if (w.x != h || offlen_len(w.y) != len) return false;
   if (!bytes_equal(M.ctx + offlen_off(w.y), s, len)) return false;
   *val = int64_t(w.z);
