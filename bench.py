@@ -662,6 +662,25 @@ def main():
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(a.elapsed_time(b) / e2e_steps, world, "cuda")
     assert np.array_equal(h_found.numpy(), w.expect_found)
+    # where the end-to-end time goes: the two host-buffer calls, and the host
+    # link's own pinned copy rates (outside the timed region)
+    c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    c0.record(stream)
+    m_e = F.fks_build_u64_host(h_keys, h_vals, rank_seed(rank))
+    c1.record(stream)
+    F.fks_lookup_u64_host(m_e, h_q, h_out, h_found, -1)
+    c2.record(stream)
+    torch.cuda.synchronize()
+    del m_e
+    d_tmp = torch.empty_like(keys)
+    h2d_ms = _timed(torch, stream, lambda: d_tmp.copy_(h_keys, non_blocking=True), reps=3)
+    d2h_ms = _timed(torch, stream, lambda: h_keys.copy_(d_tmp, non_blocking=True), reps=3)
+    del d_tmp
+    link = {"h2d_GBps": 8 * n / (h2d_ms / 1e3) / 1e9, "d2h_GBps": 8 * n / (d2h_ms / 1e3) / 1e9,
+            "build_host_ms": c0.elapsed_time(c1), "lookup_host_ms": c1.elapsed_time(c2)}
+    # the step cannot beat moving its bytes once over the link
+    link["link_bound_ms"] = (16 * n / (link["h2d_GBps"] * 1e9) + max(8 * nq / (link["h2d_GBps"] * 1e9),
+                                                                     9 * nq / (link["d2h_GBps"] * 1e9))) * 1e3
 
     # ---- roofline of the dominant kernel
     hbm, peak_kind = load_peaks()
@@ -721,7 +740,7 @@ def main():
                     for k, v in kernels.items()},
         "e2e": {"value": units / (e2e_ms / 1e3), "unit": "keys+lookups/s",
                 "h2d_bytes_per_step": int(8 * n + 8 * n + 8 * nq),
-                "d2h_bytes_per_step": int(8 * nq + nq), "ms_per_step": e2e_ms},
+                "d2h_bytes_per_step": int(8 * nq + nq), "ms_per_step": e2e_ms, "link": link},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "autotune": tune,
