@@ -60,6 +60,52 @@ class fks_build_profile(ctypes.Structure):
                 ("grouping_levels", ctypes.c_uint32), ("group_ms", ctypes.c_float)]
 
 
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class fks_allocator(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_size_t), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("user", ctypes.c_void_p)]
+
+
+class Allocator:
+    """A device-memory hook for the library (fks_allocator): alloc(nbytes,
+    stream) -> device pointer or 0/None, free(ptr, nbytes, stream).  Keep the
+    object alive while any map built with it exists: the library calls free
+    when the map is destroyed."""
+
+    def __init__(self, alloc, free):
+        self._alloc = ALLOC_FN(lambda n, st, u: alloc(int(n), int(st or 0)) or None)
+        self._free = FREE_FN(lambda ptr, n, st, u: free(int(ptr), int(n), int(st or 0)))
+        self.struct = fks_allocator(ctypes.sizeof(fks_allocator), self._alloc, self._free, None)
+
+    def ref(self):
+        return ctypes.byref(self.struct)
+
+
+def torch_allocator() -> Allocator:
+    """Tables and scratch from torch's caching allocator (stream-ordered on the
+    stream the library passes); an allocation failure becomes NULL, which the
+    library reports as FKS_ERR_OUT_OF_MEMORY."""
+    import torch
+
+    def alloc(n, stream):
+        try:
+            return torch.cuda.caching_allocator_alloc(n, stream=stream)
+        except RuntimeError:
+            return None
+
+    def free(ptr, n, stream):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    return Allocator(alloc, free)
+
+
+def _aref(alloc):
+    return None if alloc is None else alloc.ref()
+
+
 _lib = None
 
 
@@ -193,11 +239,11 @@ class MapSet:
             self.handle = None
 
 
-def fks_build_u64(keys, vals, seed: int, opts: fks_build_opts | None = None, stream=None) -> Map:
+def fks_build_u64(keys, vals, seed: int, opts: fks_build_opts | None = None, stream=None, alloc=None) -> Map:
     h = ctypes.c_void_p()
     n = keys.numel()
     _check(lib().fks_build_u64(_ptr(keys), _ptr(vals), _val_type(vals), n, seed & (2**64 - 1),
-                               ctypes.byref(opts) if opts else None, None, _stream(stream),
+                               ctypes.byref(opts) if opts else None, _aref(alloc), _stream(stream),
                                ctypes.byref(h)))
     return Map(h.value)
 
@@ -226,11 +272,11 @@ def fks_map_status(m: Map) -> int:
 
 
 def fks_build_bytes(ctx, offs, vals, seed: int, opts: fks_build_opts | None = None,
-                    stream=None) -> Map:
+                    stream=None, alloc=None) -> Map:
     h = ctypes.c_void_p()
     n = offs.numel() - 1
     _check(lib().fks_build_bytes(_ptr(ctx), _ptr(offs), _ptr(vals), _val_type(vals), n,
-                                 seed & (2**64 - 1), ctypes.byref(opts) if opts else None, None,
+                                 seed & (2**64 - 1), ctypes.byref(opts) if opts else None, _aref(alloc),
                                  _stream(stream), ctypes.byref(h)))
     return Map(h.value)
 
@@ -281,7 +327,7 @@ def fks_lookup_bytes(m: Map, qctx, qoffs, out_vals=None, out_found=None, absent:
 
 
 def fks_build_batched(kind: int, keys, ctx, offs, seg: np.ndarray, seeds: np.ndarray, vals,
-                      opts: fks_build_opts | None = None, stream=None, raise_on_error=True) -> MapSet:
+                      opts: fks_build_opts | None = None, stream=None, raise_on_error=True, alloc=None) -> MapSet:
     if getattr(seg, "is_cuda", False):  # device segment offsets: passed as they are
         m = seg.numel() - 1
         seg_ptr = _ptr(seg)
@@ -295,7 +341,7 @@ def fks_build_batched(kind: int, keys, ctx, offs, seg: np.ndarray, seeds: np.nda
     st = lib().fks_build_batched(kind, _ptr(keys), _ptr(ctx), _ptr(offs),
                                  seg_ptr,
                                  seeds.ctypes.data_as(ctypes.c_void_p), m, _ptr(vals),
-                                 _val_type(vals), ctypes.byref(opts) if opts else None, None,
+                                 _val_type(vals), ctypes.byref(opts) if opts else None, _aref(alloc),
                                  _stream(stream), ctypes.byref(h), status.ctypes.data_as(ctypes.c_void_p))
     s = MapSet(h.value, status)
     if raise_on_error or not h.value:
