@@ -374,6 +374,63 @@ def run_graph_builds(F, W, torch, shift=0):
     return res
 
 
+# The paper's Table 1 (an A100, Futhark; ms for 10^7 keys): construction,
+# lookup, membership.  Context for the row below, not a target.
+PAPER_TABLE1_A100_MS = {
+    "fks_u64": (18.3, 3.3, 1.6), "binary_search_u64": (40.9, 6.2, 5.8), "eytzinger_u64": (42.3, 4.3, 2.4),
+    "cucollections_u64": (2.7, 1.1, 0.9), "fks_strings": (33.2, 4.3, 2.8)}
+
+
+def run_paper_table1(F, W, torch):
+    """The paper's own evaluation setup: n = 10^7 distinct keys with int32
+    values; lookup (value + presence) and membership (presence only) of every
+    inserted key, so 100 % hits; uint64 keys, and strings of 5-25 lowercase
+    letters.  The search-based maps on the same uint64 keys."""
+    stream = torch.cuda.current_stream()
+    n = 10_000_000
+    keys_h = W.key_stream(71, n)
+    keys = torch.from_numpy(keys_h.view(np.int64)).cuda()
+    vals = torch.arange(n, dtype=torch.int32, device="cuda")
+    out = torch.empty(n, dtype=torch.int32, device="cuda")
+    found = torch.empty(n, dtype=torch.uint8, device="cuda")
+    res = {"workload": "10^7 distinct keys, int32 values, every key looked up (100 % hits)",
+           "paper_a100_ms": {k: {"build": v[0], "lookup": v[1], "membership": v[2]}
+                             for k, v in PAPER_TABLE1_A100_MS.items()}}
+
+    def row(build, lookup, member):
+        bms = _timed(torch, stream, build)
+        mp = build()
+        lms = _timed(torch, stream, lambda: lookup(mp))
+        ok = bool(found.all().item()) and bool(torch.equal(out, vals))
+        mms = _timed(torch, stream, lambda: member(mp))
+        ok = ok and bool(found.all().item())
+        del mp
+        return {"build_ms": bms, "lookup_ms": lms, "membership_ms": mms, "all_found": ok}
+
+    res["fks_u64"] = row(lambda: F.fks_build_u64(keys, vals, 7),
+                         lambda mp: F.fks_lookup_u64(mp, keys, out, found, -1),
+                         lambda mp: F.fks_lookup_u64(mp, keys, None, found, -1))
+    res["binary_search_u64"] = row(lambda: F.fks_sortmap_build(keys, vals),
+                                   lambda mp: F.fks_sortmap_lookup(mp, keys, out, found, -1),
+                                   lambda mp: F.fks_sortmap_lookup(mp, keys, None, found, -1))
+    res["eytzinger_u64"] = row(lambda: F.fks_eytzmap_build(keys, vals),
+                               lambda mp: F.fks_sortmap_lookup(mp, keys, out, found, -1),
+                               lambda mp: F.fks_sortmap_lookup(mp, keys, None, found, -1))
+    sw = W.string_workload(n, 1, 1.0, seed=72, lo=5, hi=25)
+    ctx, offs = torch.from_numpy(sw.ctx).cuda(), torch.from_numpy(sw.offs).cuda()
+    res["fks_strings"] = row(lambda: F.fks_build_bytes(ctx, offs, vals, 8),
+                             lambda mp: F.fks_lookup_bytes(mp, ctx, offs, out, found, -1),
+                             lambda mp: F.fks_lookup_bytes(mp, ctx, offs, None, found, -1))
+    for k, r in res.items():
+        if k in PAPER_TABLE1_A100_MS:
+            pb, pl, pm = PAPER_TABLE1_A100_MS[k]
+            r["vs_paper_a100"] = {"build": pb / r["build_ms"], "lookup": pl / r["lookup_ms"],
+                                  "membership": pm / r["membership_ms"]}
+    del keys, vals, out, found, ctx, offs
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_bucket_variants(F, torch, hbm, keys, vals, queries, out, found, w, n, nq, tune=True):
     """The level-one bucket-count variant on the headline workload: nb =
     ceil(n / lambda) buckets for lambda in 1, 2, 4, 8, 16 (1 is the paper's
@@ -794,6 +851,7 @@ def main():
         line["batched"] = run_batched(F, W, torch, hbm, xs)
         line["graph_builds"] = run_graph_builds(F, W, torch, xs)
         line["from_array"] = run_from_array(F, W, torch, hbm, xs)
+        line["paper_table1"] = run_paper_table1(F, W, torch)
     # ---- serving stream (config 5): continuous batching against per-call launches
     if args.serve_requests > 0:
         line["serving"] = run_serving(args, F, W, torch)

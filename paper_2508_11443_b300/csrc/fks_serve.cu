@@ -83,6 +83,7 @@ struct fks_server {
   std::condition_variable done_cv;
   std::deque<Req*> arrivals;
   std::deque<Req*> build_results;
+  std::atomic<uint64_t> posted{0};  // arrivals + build results ever queued (lets a busy scheduler skip mu)
   std::vector<Req*> all;         // every request, by ticket - 1
   std::atomic<bool> stop{false};
   // scheduler state
@@ -156,8 +157,17 @@ bool admit(fks_server* S, uint64_t need) {
 }
 
 void worker_main(fks_server* S) {
+  // Builds run at the highest stream priority: their kernels get SM slots
+  // ahead of the stream of small lookup batches, so a build shared with
+  // continuous lookups takes about as long as one alone (builds are the
+  // slowest requests, so they set the tail).
+  int least = 0, greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&least, &greatest);
   cudaStream_t st;
-  cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, greatest) != cudaSuccess) {
+    cudaGetLastError();
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  }
   for (;;) {
     Req* q = nullptr;
     {
@@ -179,6 +189,7 @@ void worker_main(fks_server* S) {
     {
       std::lock_guard<std::mutex> lk(S->mu);
       S->build_results.push_back(q);
+      S->posted.fetch_add(1, std::memory_order_release);
     }
     S->cv.notify_one();
   }
@@ -380,15 +391,20 @@ void run_one_per_call(fks_server* S, Req* q) {
 
 void scheduler_main(fks_server* S) {
   std::vector<Req*> arrivals, results;
+  uint64_t seen = 0;  // posted requests already taken from the queues
   for (;;) {
-    {
+    const bool busy = !S->inflight.empty();
+    arrivals.clear();
+    results.clear();
+    // With batches in flight the loop polls their events without sleeping
+    // (a timed wait would add the kernel's timer slack, tens of
+    // microseconds, to every completion) and takes the lock only when
+    // something was queued; idle, it sleeps until work arrives.
+    if (!busy || S->posted.load(std::memory_order_acquire) != seen) {
       std::unique_lock<std::mutex> lk(S->mu);
-      const bool busy = !S->inflight.empty();
       auto have_work = [&] { return S->stop.load() || !S->arrivals.empty() || !S->build_results.empty(); };
-      // With batches in flight the loop polls their events without sleeping
-      // (a timed wait would add the kernel's timer slack, tens of
-      // microseconds, to every completion); idle, it sleeps until work arrives.
       if (!busy) S->cv.wait(lk, have_work);
+      seen = S->posted.load(std::memory_order_relaxed);  // everything up to here is in the queues
       arrivals.assign(S->arrivals.begin(), S->arrivals.end());
       S->arrivals.clear();
       results.assign(S->build_results.begin(), S->build_results.end());
@@ -463,6 +479,7 @@ fks_status fks_server_submit(fks_server_t S, const fks_request* r, uint64_t* h_t
     S->all.push_back(q);
     q->ticket = S->all.size();
     S->arrivals.push_back(q);
+    S->posted.fetch_add(1, std::memory_order_release);
   }
   if (h_ticket) *h_ticket = q->ticket;
   S->cv.notify_one();
