@@ -157,17 +157,8 @@ bool admit(fks_server* S, uint64_t need) {
 }
 
 void worker_main(fks_server* S) {
-  // Builds run at the highest stream priority: their kernels get SM slots
-  // ahead of the stream of small lookup batches, so a build shared with
-  // continuous lookups takes about as long as one alone (builds are the
-  // slowest requests, so they set the tail).
-  int least = 0, greatest = 0;
-  cudaDeviceGetStreamPriorityRange(&least, &greatest);
   cudaStream_t st;
-  if (cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, greatest) != cudaSuccess) {
-    cudaGetLastError();
-    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-  }
+  cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
   for (;;) {
     Req* q = nullptr;
     {
