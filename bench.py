@@ -732,8 +732,22 @@ def main():
     d_tmp = torch.empty_like(keys)
     h2d_ms = _timed(torch, stream, lambda: d_tmp.copy_(h_keys, non_blocking=True), reps=3)
     d2h_ms = _timed(torch, stream, lambda: h_keys.copy_(d_tmp, non_blocking=True), reps=3)
+    # both directions at once (what the chunked host lookup needs)
+    s_up, s_dn = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def both():
+        s_up.wait_stream(stream)
+        s_dn.wait_stream(stream)
+        with torch.cuda.stream(s_up):
+            d_tmp.copy_(h_keys, non_blocking=True)
+        with torch.cuda.stream(s_dn):
+            h_out.copy_(out, non_blocking=True)
+        stream.wait_stream(s_up)
+        stream.wait_stream(s_dn)
+    bidir_ms = _timed(torch, stream, both, reps=3)
     del d_tmp
     link = {"h2d_GBps": 8 * n / (h2d_ms / 1e3) / 1e9, "d2h_GBps": 8 * n / (d2h_ms / 1e3) / 1e9,
+            "both_directions_GBps": (8 * n + 8 * nq) / (bidir_ms / 1e3) / 1e9,
             "build_host_ms": c0.elapsed_time(c1), "lookup_host_ms": c1.elapsed_time(c2)}
     # the step cannot beat moving its bytes once over the link
     link["link_bound_ms"] = (16 * n / (link["h2d_GBps"] * 1e9) + max(8 * nq / (link["h2d_GBps"] * 1e9),
