@@ -99,6 +99,47 @@ __global__ void __launch_bounds__(256) k_fingerprints(const uint8_t* __restrict_
   }
 }
 
+// The same for a one-map pass: a string longer than kLongString bytes is
+// fingerprinted by the whole warp (lanes take its words), so that it does
+// not hold up the other lanes for its whole length; shorter ones by their
+// own lane.
+__global__ void __launch_bounds__(256, 8) k_fingerprints_map(const uint8_t* __restrict__ ctx,
+                                                           const int64_t* __restrict__ offs,
+                                                           const MapDev* __restrict__ maps, uint64_t total,
+                                                           uint64_t* __restrict__ fps, MapStatus* status) {
+  __shared__ uint64_t pw[33];
+  const uint64_t key_begin = maps[0].key_begin, pass_begin = maps[0].pass_begin;
+  if (threadIdx.x < 33) pw[threadIdx.x] = pow61(maps[0].fpb, threadIdx.x);
+  __syncthreads();
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint64_t nwarps = uint64_t(gridDim.x) * (blockDim.x >> 5);
+  for (uint64_t base = (uint64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < total;
+       base += nwarps * 32) {
+    const uint64_t e = base + lane;
+    const uint64_t in = key_begin + (e - pass_begin);
+    int64_t o0 = 0, o1 = 0;
+    if (e < total) {
+      o0 = __ldg(reinterpret_cast<const long long*>(offs) + in);
+      o1 = __ldg(reinterpret_cast<const long long*>(offs) + in + 1);
+    }
+    const int64_t len = o1 - o0;
+    const bool bad = e < total && (o0 < 0 || len < 0 || len >= (int64_t(1) << 24) || o1 >= (int64_t(1) << 40));
+    if (bad) atomicExch(&status[0].invalid, 1u);
+    const bool ok = e < total && !bad;
+    const bool lng = ok && uint64_t(len) > kLongString;
+    uint64_t fp = 0;
+    if (ok && !lng) fp = fingerprint(ctx + o0, uint32_t(len), pw[1]);
+    for (uint32_t todo = __ballot_sync(0xFFFFFFFFu, lng); todo; todo &= todo - 1) {
+      const int j = __ffs(todo) - 1;
+      const int64_t oj = __shfl_sync(0xFFFFFFFFu, o0, j);
+      const uint32_t lj = uint32_t(__shfl_sync(0xFFFFFFFFu, len, j));
+      const uint64_t h = warp_fingerprint(ctx + oj, lj, pw);
+      if (int(lane) == j) fp = h;
+    }
+    if (e < total) fps[in] = fp;  // 0 for invalid offsets
+  }
+}
+
 // -------------------------------------------------------------- partitioning
 // Warp-aggregated claim of `count` consecutive cells of ctr[idx]: lanes with
 // the same idx share one atomic (the paper's Hist, Sec. 2.1, with atomics).
@@ -1198,8 +1239,12 @@ cudaError_t launch_fingerprints(const uint8_t* ctx, const int64_t* offs, uint64_
   (void)n;
   if (total == 0) return cudaSuccess;
   const uint64_t blocks = (total + 255) / 256;
-  k_fingerprints<<<unsigned(blocks < 65535ull * 16 ? blocks : 65535ull * 16), 256, 0, stream>>>(
-      ctx, offs, maps, pass_seg, m, total, fps, status);
+  if (m == 1)  // grid-stride over at most 8 blocks per SM: each block derives its powers of R once
+    k_fingerprints_map<<<unsigned(blocks < uint64_t(device_sm_count()) * 8 ? blocks : uint64_t(device_sm_count()) * 8),
+                         256, 0, stream>>>(ctx, offs, maps, total, fps, status);
+  else
+    k_fingerprints<<<unsigned(blocks < 65535ull * 16 ? blocks : 65535ull * 16), 256, 0, stream>>>(
+        ctx, offs, maps, pass_seg, m, total, fps, status);
   note_launches(1);
   return cudaGetLastError();
 }

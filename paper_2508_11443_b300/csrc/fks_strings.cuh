@@ -38,4 +38,57 @@ __device__ __forceinline__ bool bytes_equal(const uint8_t* a, const uint8_t* b, 
   return true;
 }
 
+// ---------------------------------------------------------------- warp-cooperative forms
+// Strings longer than this many bytes are fingerprinted and compared by the
+// whole warp; shorter ones by their own lane.
+constexpr uint32_t kLongString = 128;
+
+// a + b mod 2^61 - 1 for a, b < 2^61 - 1
+__device__ __forceinline__ uint64_t addp61(uint64_t a, uint64_t b) {
+  const uint64_t x = a + b;
+  return x >= kP61 ? x - kP61 : x;
+}
+
+// base^e mod 2^61 - 1 by squaring
+__device__ __forceinline__ uint64_t pow61(uint64_t base, uint32_t e) {
+  uint64_t r = 1;
+  while (e) {
+    if (e & 1u) r = mulmod61(r, base);
+    base = mulmod61(base, base);
+    e >>= 1;
+  }
+  return r;
+}
+
+// The fingerprint of s[0 .. len) by the whole warp (every lane passes the
+// same s, len; pw[t] = base^t for t <= 32).  Horner's value
+//   len * R^m + sum_t w_t * R^(m - 1 - t)   (m words, mod 2^61 - 1)
+// evaluated 32 words at a time: lane x multiplies word c + x by its power,
+// the warp sums the products, and the running value moves up by R^k.
+// Exact modular arithmetic: the same value as fingerprint().
+__device__ __forceinline__ uint64_t warp_fingerprint(const uint8_t* s, uint32_t len, const uint64_t* pw) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t words = (len + 3u) >> 2;
+  uint64_t h = len;
+  for (uint32_t c = 0; c < words; c += 32) {
+    const uint32_t k = words - c < 32u ? words - c : 32u;
+    uint64_t term = lane < k ? mulmod61(str_word(s, len, c + lane), pw[k - 1 - lane]) : 0ull;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) term = addp61(term, __shfl_xor_sync(0xFFFFFFFFu, term, d));
+    h = addp61(mulmod61(h, pw[k]), term);
+  }
+  return h;
+}
+
+// a[0 .. len) == b[0 .. len) by the whole warp, 32 words per step.
+__device__ __forceinline__ bool warp_bytes_equal(const uint8_t* a, const uint8_t* b, uint32_t len) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t words = (len + 3u) >> 2;
+  for (uint32_t c = 0; c < words; c += 32) {
+    const bool differ = c + lane < words && str_word(a, len, c + lane) != str_word(b, len, c + lane);
+    if (__any_sync(0xFFFFFFFFu, differ)) return false;
+  }
+  return true;
+}
+
 }  // namespace fks

@@ -128,3 +128,38 @@ def test_full_size_config3(F):
     assert_same(F, gm, om)
     del gm
     torch.cuda.empty_cache()
+
+
+def test_short_and_long_strings_in_the_same_warps(F):
+    """Strings above 128 bytes are fingerprinted and compared by the whole
+    warp, shorter ones by their lane: a mix of both in every warp, members
+    and non-members (a long non-member differing from a member only in its
+    last byte), against the oracle."""
+    rng = np.random.default_rng(11)
+    n = 6000
+    lens = rng.integers(4, 65, n)
+    longs = rng.random(n) < 0.1
+    lens[longs] = rng.integers(129, 3000, int(longs.sum()))
+    offs = np.zeros(n + 1, np.int64)
+    offs[1:] = np.cumsum(lens)
+    ctx = rng.integers(0, 256, int(offs[-1]), dtype=np.uint8)
+    vals = np.arange(n)
+    om = O.build_bytes(ctx, offs, vals, seed=12)
+    assert om.status == O.OK
+    gm = gpu_build(F, ctx, offs, vals, 12)
+    assert_same(F, gm, om)
+    # needles: every member, then each long member with its last byte changed
+    lk = np.nonzero(longs)[0]
+    pieces, qlens = [ctx], list(lens)
+    for k in lk:
+        s = ctx[offs[k]:offs[k + 1]].copy()
+        s[-1] ^= 0x5A
+        pieces.append(s)
+        qlens.append(s.size)
+    qctx = np.concatenate(pieces)
+    qoffs = np.zeros(len(qlens) + 1, np.int64)
+    qoffs[1:] = np.cumsum(qlens)
+    out, found = gpu_lookup(F, gm, qctx, qoffs)
+    oo, of = O.lookup_bytes(om, qctx, qoffs)
+    assert np.array_equal(found, of) and np.array_equal(out, oo)
+    assert found[:n].all() and not found[n:].any()
