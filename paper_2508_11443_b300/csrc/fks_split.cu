@@ -32,14 +32,30 @@ constexpr int kScanThreads = 512;
 
 __device__ __forceinline__ uint32_t lane() { return threadIdx.x & 31u; }
 
+// The j in [lo, hi) with seg[j] <= e < seg[j + 1] (seg[lo] <= e < seg[hi]).
 template <class T>
-__device__ __forceinline__ uint32_t seg_of(const T* seg, uint32_t m, uint64_t e) {
-  uint32_t lo = 0, hi = m;
+__device__ __forceinline__ uint32_t seg_in(const T* seg, uint32_t lo, uint32_t hi, uint64_t e) {
   while (hi - lo > 1) {
     const uint32_t mid = (lo + hi) >> 1;
     if (uint64_t(seg[mid]) <= e) lo = mid; else hi = mid;
   }
   return lo;
+}
+template <class T>
+__device__ __forceinline__ uint32_t seg_of(const T* seg, uint32_t m, uint64_t e) {
+  return seg_in(seg, 0u, m, e);
+}
+
+// The maps a tile [e0, e1) of a pass spans: [tj[0], tj[1]), found by one
+// thread in `seg` (which must be complete: a barrier before the call when it
+// is the shared copy) and published by a barrier after it, so that each
+// element's search covers those maps only -- most tiles lie inside one map.
+__device__ __forceinline__ void tile_maps(const PassDev& p, const uint64_t* seg, uint64_t e0, uint64_t e1,
+                                          uint32_t* tj) {
+  if (threadIdx.x == 0) {
+    tj[0] = p.m == 1 ? 0u : seg_of(seg, p.m, e0);
+    tj[1] = p.m == 1 ? 1u : seg_of(seg, p.m, e1 > e0 ? e1 - 1 : e0) + 1;
+  }
 }
 
 // ------------------------------------------------------------ element access
@@ -54,8 +70,9 @@ struct Elem {
 // it uses any of them: load_elem reads (the partition field holds the map),
 // finish_elem hashes and packs.
 template <bool kStr>
-__device__ __forceinline__ Elem<kStr> load_elem(const PassDev& p, const uint64_t* seg, uint64_t e) {
-  const uint32_t j = p.m == 1 ? 0u : seg_of(seg, p.m, e);
+__device__ __forceinline__ Elem<kStr> load_elem(const PassDev& p, const uint64_t* seg, const uint32_t* tj,
+                                                uint64_t e) {
+  const uint32_t j = p.m == 1 ? 0u : seg_in(seg, tj[0], tj[1], e);
   const MapDev& M = p.maps[j];
   const uint64_t in = M.key_begin + (e - M.pass_begin);
   Elem<kStr> x;
@@ -82,8 +99,9 @@ __device__ __forceinline__ void finish_elem(const PassDev& p, Elem<kStr>& x) {
   x.gp = M.part_begin + (reduce32(hash32(M.c1, x.key), M.nb) >> p.logB);
 }
 
-__device__ __forceinline__ uint64_t key_only(const PassDev& p, const uint64_t* seg, uint64_t e, uint32_t* j) {
-  *j = p.m == 1 ? 0u : seg_of(seg, p.m, e);
+__device__ __forceinline__ uint64_t key_only(const PassDev& p, const uint64_t* seg, const uint32_t* tj, uint64_t e,
+                                             uint32_t* j) {
+  *j = p.m == 1 ? 0u : seg_in(seg, tj[0], tj[1], e);
   const MapDev& M = p.maps[*j];
   return __ldcs(reinterpret_cast<const unsigned long long*>(p.hkeys) + M.key_begin + (e - M.pass_begin));
 }
@@ -120,16 +138,19 @@ __global__ void __launch_bounds__(kSplitThreads) k_countA(PassDev p, SplitDev s)
     seg = sh_seg;
   }
   for (uint32_t i = threadIdx.x; i < s.binsA; i += blockDim.x) hist[i] = 0;
-  __syncthreads();
   const uint32_t tile = blockIdx.x;
   const uint64_t e0 = uint64_t(tile) * kTile, e1 = min(p.total, e0 + kTile);
+  __shared__ uint32_t tj[2];
+  __syncthreads();  // sh_seg is complete before thread 0 searches it
+  tile_maps(p, seg, e0, e1, tj);
+  __syncthreads();
   constexpr uint32_t kPer = kTile / kSplitThreads;
   uint64_t k[kPer];
   uint32_t jm[kPer];
 #pragma unroll
   for (uint32_t u = 0; u < kPer; ++u) {  // all loads first
     const uint64_t e = e0 + threadIdx.x + u * kSplitThreads;
-    k[u] = e < e1 ? key_only(p, seg, e, &jm[u]) : 0ull;
+    k[u] = e < e1 ? key_only(p, seg, tj, e, &jm[u]) : 0ull;
   }
 #pragma unroll
   for (uint32_t u = 0; u < kPer; ++u) {
@@ -159,8 +180,11 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_scatterA(PassDev p, SplitD
     cur[i] = 0;
     dbase[i] = s.histA[uint64_t(i) * s.tilesA + tile];  // this tile's output start per bin
   }
-  __syncthreads();
   const uint64_t e0 = uint64_t(tile) * kTile, e1 = min(p.total, e0 + kTile);
+  __shared__ uint32_t tj[2];
+  __syncthreads();  // sh_seg is complete before thread 0 searches it
+  tile_maps(p, seg, e0, e1, tj);
+  __syncthreads();
   const uint32_t cnt = uint32_t(e1 - e0);
   constexpr uint32_t kPer = kTile / kSplitThreads;
   Elem<kStr> x[kPer];
@@ -168,7 +192,7 @@ __global__ void __launch_bounds__(kSplitThreads, 2) k_scatterA(PassDev p, SplitD
 #pragma unroll
   for (uint32_t u = 0; u < kPer; ++u) {  // all loads first
     const uint32_t i = threadIdx.x + u * kSplitThreads;
-    if (i < cnt) x[u] = load_elem<kStr>(p, seg, e0 + i);
+    if (i < cnt) x[u] = load_elem<kStr>(p, seg, tj, e0 + i);
   }
 #pragma unroll
   for (uint32_t u = 0; u < kPer; ++u) {
