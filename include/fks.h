@@ -281,7 +281,7 @@ void fks_build_graph_destroy(fks_build_graph_t g);
  * this mapping to its compiler; here it is measured.
  *
  *   thread_search_max      buckets of 2 .. T keys are searched by one thread
- *                          each (a register bitmap of the s^2 slots); larger
+ *                          each (pairwise compares of their slot indices); larger
  *                          ones by a warp segment of 2^ceil(log2 s) lanes,
  *                          above 32 keys by the whole CTA: the threads per
  *                          bucket and the small / large bucket threshold (1..3)

@@ -3,8 +3,8 @@
 //
 // A shape fixes how the work is spread over the GPU, never what is computed:
 //   build   thread_max         buckets of 2 .. thread_max keys are searched by
-//                              one thread each (a register bitmap of the s^2
-//                              slots); larger buckets by a warp segment of
+//                              one thread each (pairwise compares of the
+//                              slot indices); larger buckets by a warp segment of
 //                              2^ceil(log2 s) lanes, above 32 keys by the CTA
 //                              (threads per bucket, and the small / large
 //                              bucket threshold)
