@@ -272,7 +272,7 @@ def _timed(torch, stream, fn, reps=3, warm=1):
 
 
 def run_strings(F, W, torch, hbm, shift=0):
-    """Config 3: 2^22 distinct strings (lengths uniform in [4, 64], a-z) with
+    """String keys: 2^22 distinct strings (lengths uniform in [4, 64], a-z) with
     int32 values; 2^24 needles, 50 % members."""
     w = W.string_workload(1 << (22 - shift), 1 << (24 - shift), 0.5, seed=3)
     ctx, offs = torch.from_numpy(w.ctx).cuda(), torch.from_numpy(w.offs).cuda()
@@ -303,7 +303,7 @@ def run_strings(F, W, torch, hbm, shift=0):
 
 
 def run_batched(F, W, torch, hbm, shift=0):
-    """Config 4: 1024 maps of log-uniform size in [16, 2^20] built by one
+    """Batched maps: 1024 maps of log-uniform size in [16, 2^20] built by one
     batched call; 2^24 (map_id, key) lookups at 75 % hits."""
     b = W.batched_workload(1024 >> shift, 16, 1 << (20 - shift), 1 << (24 - shift), 0.75, seed=4)
     keys = torch.from_numpy(b.keys.view(np.int64)).cuda()
@@ -331,12 +331,12 @@ def run_batched(F, W, torch, hbm, shift=0):
 def run_graph_builds(F, W, torch, shift=0):
     """Batched builds as one recorded CUDA graph (fks_build_graph_run) against
     the same batched build launched pass by pass (fks_build_batched) and, for
-    small maps, against one fks_build_u64 call per map: config 4's 1024 maps
+    small maps, against one fks_build_u64 call per map: the 1024 batched maps
     of log-uniform size in [16, 2^20], and 2048 small maps of log-uniform size
     in [16, 4096], where launch and synchronisation costs dominate."""
     stream = torch.cuda.current_stream()
     res = {}
-    for name, m, lo, hi, per_call in (("config4_1024_maps", 1024 >> shift, 16, 1 << (20 - shift), False),
+    for name, m, lo, hi, per_call in (("batched_1024_maps", 1024 >> shift, 16, 1 << (20 - shift), False),
                                       ("small_2048_maps", 2048 >> shift, 16, 4096, True)):
         b = W.batched_workload(m, lo, hi, 16, 0.75, seed=4)
         keys = torch.from_numpy(b.keys.view(np.int64)).cuda()
@@ -505,7 +505,7 @@ def run_from_array(F, W, torch, hbm, shift=0):
 
 
 def run_serving(args, F, W, torch):
-    """Config 5: a Poisson stream of build and lookup requests (90 % lookups of
+    """Serving: a Poisson stream of build and lookup requests (90 % lookups of
     log-uniform size in [1, 2^16], 80 % hits; 10 % builds, half uint64 maps of
     log-uniform size in [2^10, 2^22], half string maps in [2^10, 2^20]) over
     maps resident under a 40 GB budget with LRU eviction, after 64 prefill
@@ -856,7 +856,7 @@ def main():
                           "build_ms": med(eb), "lookup_ms": med(el),
                           "lookups_per_s": nq / (med(el) / 1e3),
                           "fks_speedup_build": med(eb) / med(build_ms), "fks_speedup_lookup": med(el) / lk}}
-    # ---- the other rows of the path: string keys (config 3), batched maps (config 4)
+    # ---- the other rows of the path: string keys, batched maps, recorded graphs, from_array
     if not args.no_extras:
         line["bucket_variants"] = run_bucket_variants(F, torch, hbm, keys, vals, queries, out, found, w, n, nq,
                                                       tune=not (args.no_autotune or args.tuning))
@@ -866,7 +866,7 @@ def main():
         line["graph_builds"] = run_graph_builds(F, W, torch, xs)
         line["from_array"] = run_from_array(F, W, torch, hbm, xs)
         line["paper_table1"] = run_paper_table1(F, W, torch)
-    # ---- serving stream (config 5): continuous batching against per-call launches
+    # ---- serving stream: continuous batching against per-call launches
     if args.serve_requests > 0:
         line["serving"] = run_serving(args, F, W, torch)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -123,7 +123,7 @@ def test_batched_strings(F):
     assert np.array_equal(out.cpu().numpy().astype(np.int64), np.where(ef == 1, ev, -1))
 
 
-def test_full_size_config4(F):
+def test_full_size_1024_maps(F):
     """1024 maps, n log-uniform in [16, 2^20] (about 10^8 keys), 2^24 batched
     lookups at 75 % hits: every lookup against the workload's truth, and the
     tables of a sample of maps (the smallest, the largest and 14 others)

@@ -115,7 +115,7 @@ def test_long_and_binary_strings(F):
     assert found.all() and np.array_equal(out, np.arange(lens.size))
 
 
-def test_full_size_config3(F):
+def test_full_size_2e22_strings(F):
     """2^22 distinct strings (lengths 4..64, a-z), 2^24 needles at 50 % hits."""
     import torch
     w = W.string_workload(1 << 22, 1 << 24, 0.5, seed=3)

@@ -72,7 +72,7 @@ def test_tables_and_lookups_bit_exact(F, n):
     assert np.array_equal(found, w.expect_found)
 
 
-def test_config1_workload(F):
+def test_2e16_keys_half_hits_workload(F):
     """2^16 keys, 2^16 queries with 50 % members."""
     w = W.u64_workload(1 << 16, 1 << 16, 0.5, seed=1)
     om = O.build_u64(w.keys, w.vals, seed=1)
@@ -256,7 +256,7 @@ def test_invalid_arguments(F):
                         F.make_opts(bound_factor=65))
 
 
-def test_full_size_config2_bit_exact(F):
+def test_full_size_2e26_keys_bit_exact(F):
     """2^26 keys, 2^26 queries at 90 % hits, the benchmark's launch
     configuration: whole tables and every lookup output against the oracle."""
     import torch
