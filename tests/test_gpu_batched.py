@@ -144,3 +144,25 @@ def test_full_size_1024_maps(F):
         assert np.array_equal(d, om.desc) and np.array_equal(s, om.slots), j
     del S
     torch.cuda.empty_cache()
+
+
+def test_more_maps_than_the_shared_segment_table(F):
+    """3000 maps (the grouping keeps at most 2048 segment offsets in shared
+    memory; beyond that it searches them in global memory), over 2^20 keys in
+    all (two radix levels): sampled maps against the oracle, every lookup
+    against the workload's truth."""
+    import torch
+    b = W.batched_workload(3000, 100, 2000, 1 << 18, 0.75, seed=77)
+    assert b.seg_offs[-1] >= (1 << 20)
+    S = F.fks_build_batched(F.FKS_KEY_U64, dev(b.keys), None, None, b.seg_offs, b.seeds, dev(b.vals))
+    assert (S.status == 0).all() and len(S) == 3000
+    for j in (0, 1, 1499, 2047, 2048, 2999):
+        k = b.keys[b.seg_offs[j]:b.seg_offs[j + 1]]
+        om = O.build_u64(k, b.vals[b.seg_offs[j]:b.seg_offs[j + 1]], seed=int(b.seeds[j]))
+        d, s = export(F, S.get(j))
+        assert np.array_equal(d, om.desc) and np.array_equal(s, om.slots), j
+    out, found = batched_lookup(F, S, b.q_map, b.q_keys)
+    assert np.array_equal(found, b.expect_found)
+    assert np.array_equal(out, np.where(b.expect_found == 1, b.expect_vals, -1))
+    del S
+    torch.cuda.empty_cache()
