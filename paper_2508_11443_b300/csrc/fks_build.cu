@@ -1249,22 +1249,30 @@ cudaError_t launch_fingerprints(const uint8_t* ctx, const int64_t* offs, uint64_
   return cudaGetLastError();
 }
 
+// The partition kernels' shared-memory attribute and the partition kernel's
+// resident CTAs per SM, set up once per process (thread-safe static
+// initialisation; concurrent first builds wait for it).
 template <int PW>
-static cudaError_t launch_build_kernel(const PassDev& p, int sms, const BuildShape& shape, cudaStream_t stream) {
-  static int occ = -1;
-  const int smem = int(Smem<PW>::kBytes);
-  if (occ < 0) {
-    cudaError_t e = cudaFuncSetAttribute(k_part_build<PW>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_part_overflow<PW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             smem);
-    if (e != cudaSuccess) return e;
+struct BuildKernelSetup {
+  cudaError_t err = cudaSuccess;
+  int occ = 1;
+  BuildKernelSetup() {
+    const int smem = int(Smem<PW>::kBytes);
+    err = cudaFuncSetAttribute(k_part_build<PW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (err == cudaSuccess)
+      err = cudaFuncSetAttribute(k_part_overflow<PW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int o = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_part_build<PW>, kPartThreads, smem);
-    if (e != cudaSuccess) return e;
+    if (err == cudaSuccess) err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_part_build<PW>, kPartThreads, smem);
     occ = o > 0 ? o : 1;
   }
+};
+
+template <int PW>
+static cudaError_t launch_build_kernel(const PassDev& p, int sms, const BuildShape& shape, cudaStream_t stream) {
+  static const BuildKernelSetup<PW> setup;
+  if (setup.err != cudaSuccess) return setup.err;
+  const int occ = setup.occ;
+  const int smem = int(Smem<PW>::kBytes);
   const uint64_t per_sm = shape.part_ctas_per_sm && int(shape.part_ctas_per_sm) < occ ? shape.part_ctas_per_sm : occ;
   const uint64_t want = uint64_t(sms) * per_sm;
   const unsigned grid = unsigned(p.P < want ? p.P : want);

@@ -528,14 +528,18 @@ cudaError_t launch_split(const PassDev& p, const SplitDev& s, bool strings, cuda
   const int PW = strings ? 2 : 1;
   const size_t smemA = size_t(kTile) * 8 * (1 + PW) + size_t(kTile) * 4;
   const size_t smemB = size_t(kTile) * 8 * (1 + PW) + size_t(kTile) * 2;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_scatterA<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTile * 8 * 3 + kTile * 4));
-    cudaFuncSetAttribute(k_scatterA<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTile * 8 * 3 + kTile * 4));
-    cudaFuncSetAttribute(k_scatterB<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTile * 8 * 3 + kTile * 2));
-    cudaFuncSetAttribute(k_scatterB<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTile * 8 * 3 + kTile * 2));
-    attr = true;
-  }
+  // the scatters' shared-memory attribute, set once per process (thread-safe
+  // static initialisation; concurrent first builds wait for it)
+  static const cudaError_t attr = [] {
+    cudaError_t r = cudaSuccess;
+    const int a = int(kTile * 8 * 3 + kTile * 4), b = int(kTile * 8 * 3 + kTile * 2);
+    if (r == cudaSuccess) r = cudaFuncSetAttribute(k_scatterA<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, a);
+    if (r == cudaSuccess) r = cudaFuncSetAttribute(k_scatterA<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, a);
+    if (r == cudaSuccess) r = cudaFuncSetAttribute(k_scatterB<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    if (r == cudaSuccess) r = cudaFuncSetAttribute(k_scatterB<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    return r;
+  }();
+  if (attr != cudaSuccess) return attr;
   k_countA<<<s.tilesA, kSplitThreads, 0, st>>>(p, s);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = scan_exclusive<uint32_t>(s.histA, uint64_t(s.binsA) * s.tilesA, s.sums, st)) != cudaSuccess) return e;
