@@ -1348,7 +1348,8 @@ cudaError_t launch_dupcheck(const uint64_t* hkeys, const int64_t* offs, const ui
     return e;
   if ((e = cudaMemsetAsync(flags, 0, sizeof(uint32_t) * 4, stream)) != cudaSuccess) return e;
   uint64_t blocks = (n + 255) / 256;
-  if (blocks > 148ull * 16) blocks = 148ull * 16;
+  const uint64_t maxb = uint64_t(device_sm_count()) * 16;
+  if (blocks > maxb) blocks = maxb;
   k_dupcheck<<<unsigned(blocks), 256, 0, stream>>>(hkeys, offs, ctx, n, table, table_idx,
                                                   table_size, flags, spin_limit);
   note_launches(1);
