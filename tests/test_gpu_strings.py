@@ -163,3 +163,26 @@ def test_short_and_long_strings_in_the_same_warps(F):
     oo, of = O.lookup_bytes(om, qctx, qoffs)
     assert np.array_equal(found, of) and np.array_equal(out, oo)
     assert found[:n].all() and not found[n:].any()
+
+
+def test_strings_up_to_the_per_lane_limit(F):
+    """Lengths 5..128 bytes (the longest strings a lane still fingerprints and
+    compares alone) and one empty string, at an aligned and at an unaligned
+    context start: tables (fingerprints included) and lookups equal the
+    oracle's."""
+    rng = np.random.default_rng(41)
+    n = 20000
+    lens = rng.integers(5, 129, n)
+    lens[777] = 0
+    offs = np.zeros(n + 1, np.int64)
+    offs[1:] = np.cumsum(lens)
+    body = rng.integers(0, 256, int(offs[-1]), dtype=np.uint8)
+    vals = np.arange(n)
+    om = O.build_bytes(body, offs, vals, seed=14)
+    assert om.status == O.OK
+    for pad in (0, 3):
+        ctx_t = dev(np.concatenate([np.zeros(pad, np.uint8), body]))[pad:]
+        gm = F.fks_build_bytes(ctx_t, dev(offs), dev(vals), 14)
+        assert_same(F, gm, om)
+        out, found = gpu_lookup(F, gm, body, offs)
+        assert found.all() and np.array_equal(out, vals)
