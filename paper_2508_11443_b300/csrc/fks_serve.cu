@@ -27,6 +27,7 @@
 
 #include "fks.h"
 #include "fks_internal.cuh"
+#include "fks_testing.h"
 
 using namespace fks;
 
@@ -67,6 +68,7 @@ struct MapSlot {
 
 struct Batch {
   cudaEvent_t ev = nullptr;
+  cudaError_t err = cudaSuccess;  // a failed upload or launch: the batch's requests fail
   std::vector<Req*> reqs;
   LookupReq* h_reqs = nullptr;  // pinned
   uint64_t* h_begins = nullptr;
@@ -277,6 +279,16 @@ void apply_build_result(fks_server* S, Req* q) {
   complete(S, q, q->status);
 }
 
+// failure injection (fks_testing.h): lookup batches left to fail at launch
+std::atomic<int> g_fail_serve_launches{0};
+
+bool inject_launch_failure() {
+  int n = g_fail_serve_launches.load();
+  while (n > 0 && !g_fail_serve_launches.compare_exchange_weak(n, n - 1)) {
+  }
+  return n > 0;
+}
+
 void launch_batches(fks_server* S) {
   while (!S->ready.empty() && S->inflight.size() < S->opts.max_inflight_batches && !S->idle_batches.empty()) {
     Batch* b = S->idle_batches.back();
@@ -303,10 +315,17 @@ void launch_batches(fks_server* S) {
       total += q->r.nq;
     }
     b->h_begins[take] = total;
-    cudaMemcpyAsync(b->d_reqs, b->h_reqs, sizeof(LookupReq) * take, cudaMemcpyHostToDevice, S->stream);
-    cudaMemcpyAsync(b->d_begins, b->h_begins, sizeof(uint64_t) * (take + 1), cudaMemcpyHostToDevice, S->stream);
-    launch_lookup_requests(b->d_reqs, b->d_begins, uint32_t(take), total, S->sms, S->stream);
-    cudaEventRecord(b->ev, S->stream);
+    cudaError_t e = cudaMemcpyAsync(b->d_reqs, b->h_reqs, sizeof(LookupReq) * take, cudaMemcpyHostToDevice,
+                                    S->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->d_begins, b->h_begins, sizeof(uint64_t) * (take + 1), cudaMemcpyHostToDevice,
+                          S->stream);
+    if (e == cudaSuccess)
+      e = inject_launch_failure() ? cudaErrorLaunchFailure
+                                  : launch_lookup_requests(b->d_reqs, b->d_begins, uint32_t(take), total, S->sms,
+                                                           S->stream);
+    const cudaError_t er = cudaEventRecord(b->ev, S->stream);
+    b->err = e != cudaSuccess ? e : er;
     S->inflight.push_back(b);
     ++S->batches;
   }
@@ -315,9 +334,11 @@ void launch_batches(fks_server* S) {
 void poll_batches(fks_server* S) {
   while (!S->inflight.empty()) {
     Batch* b = S->inflight.front();
-    const cudaError_t e = cudaEventQuery(b->ev);
+    const cudaError_t e = b->err != cudaSuccess ? b->err : cudaEventQuery(b->ev);
     if (e == cudaErrorNotReady) break;
     const fks_status st = e == cudaSuccess ? FKS_OK : FKS_ERR_CUDA;
+    if (b->err != cudaSuccess) cudaStreamSynchronize(S->stream);  // nothing of the batch still reads its buffers
+    b->err = cudaSuccess;
     for (Req* q : b->reqs) {
       lookup_done(S, q);
       complete(S, q, st);
@@ -419,6 +440,8 @@ void scheduler_main(fks_server* S) {
 }  // namespace
 
 extern "C" {
+
+void fks_test_fail_serve_launches(int n) { g_fail_serve_launches.store(n > 0 ? n : 0); }
 
 fks_status fks_server_create(const fks_server_opts* o, fks_server_t* out) {
   if (!out || !o || o->struct_size < sizeof(fks_server_opts) || o->max_maps == 0 || o->memory_budget == 0 ||

@@ -164,6 +164,8 @@ def lib():
         L.fks_kernel_launches.restype = u64
         L.fks_test_hold_first_partition.argtypes = [ctypes.c_int]
         L.fks_test_hold_first_partition.restype = None
+        L.fks_test_fail_serve_launches.argtypes = [ctypes.c_int]
+        L.fks_test_fail_serve_launches.restype = None
         for name in ("fks_build_u64", "fks_build_bytes", "fks_lookup_u64", "fks_lookup_bytes",
                      "fks_build_batched", "fks_lookup_batched", "fks_map_info", "fks_map_export"):
             getattr(L, name).restype = st
@@ -776,3 +778,7 @@ def fks_kernel_launches() -> int:
 
 def fks_test_hold_first_partition(on: bool):
     lib().fks_test_hold_first_partition(1 if on else 0)
+
+
+def fks_test_fail_serve_launches(n: int):
+    lib().fks_test_fail_serve_launches(int(n))

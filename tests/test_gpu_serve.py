@@ -145,3 +145,37 @@ def test_lru_eviction_admission_and_parked_lookups(F):
     assert F.fks_server_wait(srv, t)[0] == F.FKS_ERR_OUT_OF_MEMORY
     assert F.fks_server_stats(srv).rejected == 1
     srv.close()
+
+
+def test_a_failed_batch_launch_fails_its_requests_only(F):
+    """A lookup batch whose launch fails (injected on the host: the launch is
+    not issued and reports a launch error) completes each of its requests
+    with FKS_ERR_CUDA; the server, the context and the next batches are
+    unaffected."""
+    import torch
+    keys = torch.from_numpy(W.key_stream(300, 5000).view(np.int64)).cuda()
+    vals = torch.arange(5000, dtype=torch.int64, device="cuda")
+    out = torch.full((5000,), 7, dtype=torch.int64, device="cuda")
+    found = torch.zeros(5000, dtype=torch.uint8, device="cuda")
+    srv = F.fks_server_create(memory_budget=1 << 30, max_maps=2)
+    try:
+        t = F.fks_server_submit(srv, F.make_request(type=F.FKS_REQ_BUILD, map_id=0, key_kind=0,
+                                                    val_type=F.FKS_VAL_I64, keys=keys.data_ptr(),
+                                                    vals=vals.data_ptr(), n=5000, seed=3))
+        assert F.fks_server_wait(srv, t)[0] == F.FKS_OK
+
+        def lookup():
+            return F.fks_server_submit(srv, F.make_request(type=F.FKS_REQ_LOOKUP, map_id=0, key_kind=0,
+                                                           q=keys.data_ptr(), nq=5000, out_vals=out.data_ptr(),
+                                                           out_found=found.data_ptr(), absent=-1))
+
+        F.fks_test_fail_serve_launches(1)
+        assert F.fks_server_wait(srv, lookup())[0] == F.FKS_ERR_CUDA
+        torch.cuda.synchronize()
+        assert (out.cpu().numpy() == 7).all() and not found.cpu().numpy().any()  # nothing was written
+        assert F.fks_server_wait(srv, lookup())[0] == F.FKS_OK
+        torch.cuda.synchronize()
+        assert found.cpu().numpy().all() and np.array_equal(out.cpu().numpy(), np.arange(5000))
+    finally:
+        F.fks_test_fail_serve_launches(0)
+        srv.close()
