@@ -258,7 +258,8 @@ cudaError_t launch_sort_pairs(const uint64_t* keys, const uint64_t* vals, uint64
 
 cudaError_t launch_widen_i32(const int32_t* in, uint64_t n, uint64_t* out, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  k_widen_i32<<<1184, 256, 0, st>>>(in, n, out);
+  const uint64_t blocks = (n + 255) / 256, cap = uint64_t(device_sm_count()) * 8;
+  k_widen_i32<<<unsigned(blocks < cap ? blocks : cap), 256, 0, st>>>(in, n, out);
   note_launches(1);
   return cudaGetLastError();
 }

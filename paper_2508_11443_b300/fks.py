@@ -178,8 +178,28 @@ def _check(status: int):
         raise FksError(status, lib().fks_last_error().decode())
 
 
-def _ptr(t):
-    return None if t is None else ctypes.c_void_p(t.data_ptr())
+def _ptr(t, name="buffer", itemsize=None, numel=None):
+    """Device address of a tensor (None passes NULL), after the checks the C
+    ABI cannot make on a bare pointer: CUDA memory, dense, of the element
+    width the call reads or writes, and at least as long as it needs."""
+    if t is None:
+        return None
+    if not getattr(t, "is_cuda", False):
+        raise TypeError(f"{name}: a CUDA tensor is expected")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: a contiguous tensor is expected")
+    if itemsize is not None and t.element_size() != itemsize:
+        raise TypeError(f"{name}: elements of {itemsize} bytes are expected, got {t.dtype}")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name}: at least {numel} elements are expected, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _outs(out_vals, out_found, nq: int, value_bytes):
+    """Result buffers of a lookup of nq needles: values of the map's width
+    (value_bytes() is asked only when values are requested), flags of 1 byte."""
+    v = None if out_vals is None else _ptr(out_vals, "out_vals", value_bytes(), nq)
+    return v, _ptr(out_found, "out_found", 1, nq)
 
 
 def _stream(stream):
@@ -209,12 +229,18 @@ def make_opts(**kw) -> fks_build_opts:
 class Map:
     """Owning handle of a built map (destroyed with the object)."""
 
-    def __init__(self, handle: int, owner=None):
+    def __init__(self, handle: int, owner=None, vbytes: int | None = None):
         self.handle = handle
         self._owner = owner  # a MapSet for borrowed handles
+        self._vbytes = vbytes  # bytes of a value (4 or 8); asked from the map when unknown
 
     def info(self) -> fks_map_info_t:
         return fks_map_info(self)
+
+    def value_bytes(self) -> int:
+        if self._vbytes is None:
+            self._vbytes = 8 if fks_map_info(self).val_type == FKS_VAL_I64 else 4
+        return self._vbytes
 
     def __del__(self):
         if self._owner is None and self.handle and _lib is not None:
@@ -223,17 +249,18 @@ class Map:
 
 
 class MapSet:
-    def __init__(self, handle: int, status: np.ndarray, owned: bool = True):
+    def __init__(self, handle: int, status: np.ndarray, owned: bool = True, vbytes: int | None = None):
         self.handle = handle
         self.status = status
         self._owned = owned  # False: the set of a recorded build, freed with it
+        self.vbytes = vbytes  # bytes of a value of every map of the set
 
     def __len__(self):
         return int(lib().fks_mapset_size(self.handle))
 
     def get(self, j: int):
         h = lib().fks_mapset_get(self.handle, j)
-        return Map(h, owner=self) if h else None
+        return Map(h, owner=self, vbytes=self.vbytes) if h else None
 
     def __del__(self):
         if self._owned and self.handle and _lib is not None:
@@ -244,27 +271,29 @@ class MapSet:
 def fks_build_u64(keys, vals, seed: int, opts: fks_build_opts | None = None, stream=None, alloc=None) -> Map:
     h = ctypes.c_void_p()
     n = keys.numel()
-    _check(lib().fks_build_u64(_ptr(keys), _ptr(vals), _val_type(vals), n, seed & (2**64 - 1),
-                               ctypes.byref(opts) if opts else None, _aref(alloc), _stream(stream),
-                               ctypes.byref(h)))
-    return Map(h.value)
+    _check(lib().fks_build_u64(_ptr(keys, "keys", 8), _ptr(vals, "vals", None, n), _val_type(vals), n,
+                               seed & (2**64 - 1), ctypes.byref(opts) if opts else None, _aref(alloc),
+                               _stream(stream), ctypes.byref(h)))
+    return Map(h.value, vbytes=vals.element_size())
 
 
 def fks_build_u64_async(keys, vals, seed: int, opts: fks_build_opts | None = None, stream=None) -> Map:
     """Start a build and return its handle at once; fks_map_info reports the outcome."""
     h = ctypes.c_void_p()
-    _check(lib().fks_build_u64_async(_ptr(keys), _ptr(vals), _val_type(vals), keys.numel(), seed & (2**64 - 1),
+    _check(lib().fks_build_u64_async(_ptr(keys, "keys", 8), _ptr(vals, "vals", None, keys.numel()),
+                                     _val_type(vals), keys.numel(), seed & (2**64 - 1),
                                      ctypes.byref(opts) if opts else None, None, _stream(stream),
                                      ctypes.byref(h)))
-    return Map(h.value)
+    return Map(h.value, vbytes=vals.element_size())
 
 
 def fks_build_bytes_async(ctx, offs, vals, seed: int, opts: fks_build_opts | None = None, stream=None) -> Map:
     h = ctypes.c_void_p()
-    _check(lib().fks_build_bytes_async(_ptr(ctx), _ptr(offs), _ptr(vals), _val_type(vals), offs.numel() - 1,
-                                       seed & (2**64 - 1), ctypes.byref(opts) if opts else None, None,
-                                       _stream(stream), ctypes.byref(h)))
-    return Map(h.value)
+    _check(lib().fks_build_bytes_async(_ptr(ctx, "ctx", 1), _ptr(offs, "offs", 8, 1),
+                                       _ptr(vals, "vals", None, offs.numel() - 1), _val_type(vals),
+                                       offs.numel() - 1, seed & (2**64 - 1), ctypes.byref(opts) if opts else None,
+                                       None, _stream(stream), ctypes.byref(h)))
+    return Map(h.value, vbytes=vals.element_size())
 
 
 def fks_map_status(m: Map) -> int:
@@ -277,25 +306,35 @@ def fks_build_bytes(ctx, offs, vals, seed: int, opts: fks_build_opts | None = No
                     stream=None, alloc=None) -> Map:
     h = ctypes.c_void_p()
     n = offs.numel() - 1
-    _check(lib().fks_build_bytes(_ptr(ctx), _ptr(offs), _ptr(vals), _val_type(vals), n,
-                                 seed & (2**64 - 1), ctypes.byref(opts) if opts else None, _aref(alloc),
-                                 _stream(stream), ctypes.byref(h)))
-    return Map(h.value)
+    _check(lib().fks_build_bytes(_ptr(ctx, "ctx", 1), _ptr(offs, "offs", 8, 1), _ptr(vals, "vals", None, n),
+                                 _val_type(vals), n, seed & (2**64 - 1), ctypes.byref(opts) if opts else None,
+                                 _aref(alloc), _stream(stream), ctypes.byref(h)))
+    return Map(h.value, vbytes=vals.element_size())
 
 
 def fks_lookup_u64(m: Map, q, out_vals=None, out_found=None, absent: int = -1, stream=None):
-    _check(lib().fks_lookup_u64(m.handle, _ptr(q), q.numel(), _ptr(out_vals), _ptr(out_found),
-                                absent, _stream(stream)))
+    ov, of = _outs(out_vals, out_found, q.numel(), m.value_bytes)
+    _check(lib().fks_lookup_u64(m.handle, _ptr(q, "q", 8), q.numel(), ov, of, absent, _stream(stream)))
 
 
-def _hptr(a):
-    """Host address of a CPU tensor or numpy array (None passes NULL)."""
+def _hptr(a, name="buffer", itemsize=None, numel=None):
+    """Host address of a CPU tensor or numpy array (None passes NULL), after
+    the same checks as _ptr: host memory, dense, element width, length."""
     if a is None:
         return None
     if isinstance(a, np.ndarray):
-        return ctypes.c_void_p(a.ctypes.data)
-    assert not a.is_cuda, "host buffer expected"
-    return ctypes.c_void_p(a.data_ptr())
+        dense, size, count = a.flags.c_contiguous, a.itemsize, a.size
+    else:
+        if getattr(a, "is_cuda", False):
+            raise TypeError(f"{name}: a host buffer is expected")
+        dense, size, count = a.is_contiguous(), a.element_size(), a.numel()
+    if not dense:
+        raise ValueError(f"{name}: a contiguous buffer is expected")
+    if itemsize is not None and size != itemsize:
+        raise TypeError(f"{name}: elements of {itemsize} bytes are expected")
+    if numel is not None and count < numel:
+        raise ValueError(f"{name}: at least {numel} elements are expected, got {count}")
+    return ctypes.c_void_p(a.ctypes.data if isinstance(a, np.ndarray) else a.data_ptr())
 
 
 def _hval_type(v) -> int:
@@ -311,41 +350,48 @@ def fks_build_u64_host(keys, vals, seed: int, opts: fks_build_opts | None = None
     """fks_build_u64 over host keys / values (numpy arrays or CPU tensors)."""
     h = ctypes.c_void_p()
     n = len(keys)
-    _check(lib().fks_build_u64_host(_hptr(keys), _hptr(vals), _hval_type(vals), n, seed & (2**64 - 1),
+    vt = _hval_type(vals)
+    _check(lib().fks_build_u64_host(_hptr(keys, "keys", 8), _hptr(vals, "vals", None, n), vt, n, seed & (2**64 - 1),
                                     ctypes.byref(opts) if opts else None, None, _stream(stream), ctypes.byref(h)))
-    return Map(h.value)
+    return Map(h.value, vbytes=8 if vt == FKS_VAL_I64 else 4)
 
 
 def fks_lookup_u64_host(m: Map, q, out_vals=None, out_found=None, absent: int = -1, stream=None):
     """fks_lookup_u64 over host needles and results; blocks until done."""
-    _check(lib().fks_lookup_u64_host(m.handle, _hptr(q), len(q), _hptr(out_vals), _hptr(out_found), absent,
-                                     _stream(stream)))
+    nq = len(q)
+    ov = None if out_vals is None else _hptr(out_vals, "out_vals", m.value_bytes(), nq)
+    _check(lib().fks_lookup_u64_host(m.handle, _hptr(q, "q", 8), nq, ov, _hptr(out_found, "out_found", 1, nq),
+                                     absent, _stream(stream)))
 
 
 def fks_lookup_bytes(m: Map, qctx, qoffs, out_vals=None, out_found=None, absent: int = -1,
                      stream=None):
-    _check(lib().fks_lookup_bytes(m.handle, _ptr(qctx), _ptr(qoffs), qoffs.numel() - 1,
-                                  _ptr(out_vals), _ptr(out_found), absent, _stream(stream)))
+    nq = qoffs.numel() - 1
+    ov, of = _outs(out_vals, out_found, nq, m.value_bytes)
+    _check(lib().fks_lookup_bytes(m.handle, _ptr(qctx, "qctx", 1), _ptr(qoffs, "qoffs", 8, 1), nq, ov, of,
+                                  absent, _stream(stream)))
 
 
 def fks_build_batched(kind: int, keys, ctx, offs, seg: np.ndarray, seeds: np.ndarray, vals,
                       opts: fks_build_opts | None = None, stream=None, raise_on_error=True, alloc=None) -> MapSet:
     if getattr(seg, "is_cuda", False):  # device segment offsets: passed as they are
         m = seg.numel() - 1
-        seg_ptr = _ptr(seg)
+        seg_ptr = _ptr(seg, "seg", 8, 1)
+        total = None
     else:
         seg = np.ascontiguousarray(seg, np.int64)
         m = seg.size - 1
         seg_ptr = seg.ctypes.data_as(ctypes.c_void_p)
+        total = int(seg[-1]) if seg.size else 0
     seeds = np.ascontiguousarray(seeds, np.uint64)
     status = np.zeros(m, np.int32)
     h = ctypes.c_void_p()
-    st = lib().fks_build_batched(kind, _ptr(keys), _ptr(ctx), _ptr(offs),
+    st = lib().fks_build_batched(kind, _ptr(keys, "keys", 8), _ptr(ctx, "ctx", 1), _ptr(offs, "offs", 8),
                                  seg_ptr,
-                                 seeds.ctypes.data_as(ctypes.c_void_p), m, _ptr(vals),
+                                 seeds.ctypes.data_as(ctypes.c_void_p), m, _ptr(vals, "vals", None, total),
                                  _val_type(vals), ctypes.byref(opts) if opts else None, _aref(alloc),
                                  _stream(stream), ctypes.byref(h), status.ctypes.data_as(ctypes.c_void_p))
-    s = MapSet(h.value, status)
+    s = MapSet(h.value, status, vbytes=vals.element_size())
     if raise_on_error or not h.value:
         _check(st)
     return s
@@ -354,8 +400,10 @@ def fks_build_batched(kind: int, keys, ctx, offs, seg: np.ndarray, seeds: np.nda
 def fks_lookup_batched(s: MapSet, map_ids, q=None, qctx=None, qoffs=None, out_vals=None,
                        out_found=None, absent: int = -1, stream=None):
     nq = map_ids.numel()
-    _check(lib().fks_lookup_batched(s.handle, _ptr(map_ids), _ptr(q), _ptr(qctx), _ptr(qoffs), nq,
-                                    _ptr(out_vals), _ptr(out_found), absent, _stream(stream)))
+    ov, of = _outs(out_vals, out_found, nq, lambda: s.vbytes if s.vbytes else 8)
+    _check(lib().fks_lookup_batched(s.handle, _ptr(map_ids, "map_ids", 4), _ptr(q, "q", 8, nq),
+                                    _ptr(qctx, "qctx", 1), _ptr(qoffs, "qoffs", 8, nq + 1), nq, ov, of, absent,
+                                    _stream(stream)))
 
 
 class BuildGraph:
@@ -369,7 +417,8 @@ class BuildGraph:
     def mapset(self) -> MapSet:
         """The maps of the last run (owned by the graph)."""
         h = _graph_lib().fks_build_graph_mapset(self.handle)
-        s = MapSet(h, self.status, owned=False)
+        vals = self._inputs[3]
+        s = MapSet(h, self.status, owned=False, vbytes=vals.element_size())
         s._graph = self  # the graph must outlive the set's use
         return s
 
@@ -409,8 +458,9 @@ def fks_build_graph_create(kind: int, keys, ctx, offs, seg: np.ndarray, vals,
     seg = np.ascontiguousarray(seg, np.int64)
     m = seg.size - 1
     h = ctypes.c_void_p()
-    _check(_graph_lib().fks_build_graph_create(kind, _ptr(keys), _ptr(ctx), _ptr(offs),
-                                               seg.ctypes.data_as(ctypes.c_void_p), m, _ptr(vals),
+    _check(_graph_lib().fks_build_graph_create(kind, _ptr(keys, "keys", 8), _ptr(ctx, "ctx", 1),
+                                               _ptr(offs, "offs", 8), seg.ctypes.data_as(ctypes.c_void_p), m,
+                                               _ptr(vals, "vals", None, int(seg[-1]) if seg.size else 0),
                                                _val_type(vals), ctypes.byref(opts) if opts else None, None,
                                                _stream(stream), ctypes.byref(h)))
     return BuildGraph(h.value, (keys, ctx, offs, vals), m)
@@ -529,8 +579,9 @@ def fks_build_u64_noalloc(keys, vals, seed: int, desc_out, slots_out,
                   ctypes.POINTER(fks_map_info_t), ctypes.c_void_p]
     f.restype = ctypes.c_int
     info = fks_map_info_t()
-    st = f(_ptr(keys), _ptr(vals), _val_type(vals), keys.numel(), seed & (2**64 - 1),
-           ctypes.byref(opts) if opts else None, _ptr(desc_out), _ptr(slots_out),
+    st = f(_ptr(keys, "keys", 8), _ptr(vals, "vals", None, keys.numel()), _val_type(vals), keys.numel(),
+           seed & (2**64 - 1), ctypes.byref(opts) if opts else None, _ptr(desc_out, "desc_out", 8),
+           _ptr(slots_out, "slots_out", 8),
            slots_out.numel() // 2, ctypes.byref(info), _stream(stream))
     if st != FKS_OK:
         raise FksError(st, fks_status_str(st))
@@ -574,7 +625,7 @@ def fks_map_import(info: fks_map_info_t, desc: np.ndarray, slots: np.ndarray, ct
     h = ctypes.c_void_p()
     _check(L.fks_map_import(ctypes.byref(info), desc.ctypes.data_as(ctypes.c_void_p),
                             slots.ctypes.data_as(ctypes.c_void_p), cptr, None, _stream(stream), ctypes.byref(h)))
-    return Map(h.value)
+    return Map(h.value, vbytes=8 if info.val_type == FKS_VAL_I64 else 4)
 
 
 def fks_map_save(m: Map, path: str, stream=None):
@@ -598,8 +649,8 @@ def fks_map_load(path: str, stream=None) -> Map:
 class SortMap:
     """Owning handle of a sorted-array map (the search-based comparison)."""
 
-    def __init__(self, handle: int, n: int):
-        self.handle, self.n = handle, n
+    def __init__(self, handle: int, n: int, vbytes: int = 8):
+        self.handle, self.n, self.vbytes = handle, n, vbytes
 
     def __del__(self):
         if self.handle and _lib is not None:
@@ -609,21 +660,21 @@ class SortMap:
 
 def fks_sortmap_build(keys, vals, stream=None) -> SortMap:
     h = ctypes.c_void_p()
-    _check(lib().fks_sortmap_build(_ptr(keys), _ptr(vals), _val_type(vals), keys.numel(), None,
-                                   _stream(stream), ctypes.byref(h)))
-    return SortMap(h.value, keys.numel())
+    _check(lib().fks_sortmap_build(_ptr(keys, "keys", 8), _ptr(vals, "vals", None, keys.numel()),
+                                   _val_type(vals), keys.numel(), None, _stream(stream), ctypes.byref(h)))
+    return SortMap(h.value, keys.numel(), vals.element_size())
 
 
 def fks_eytzmap_build(keys, vals, stream=None) -> SortMap:
     h = ctypes.c_void_p()
-    _check(lib().fks_eytzmap_build(_ptr(keys), _ptr(vals), _val_type(vals), keys.numel(), None,
-                                   _stream(stream), ctypes.byref(h)))
-    return SortMap(h.value, keys.numel())
+    _check(lib().fks_eytzmap_build(_ptr(keys, "keys", 8), _ptr(vals, "vals", None, keys.numel()),
+                                   _val_type(vals), keys.numel(), None, _stream(stream), ctypes.byref(h)))
+    return SortMap(h.value, keys.numel(), vals.element_size())
 
 
 def fks_sortmap_lookup(m: SortMap, q, out_vals=None, out_found=None, absent: int = -1, stream=None):
-    _check(lib().fks_sortmap_lookup(m.handle, _ptr(q), q.numel(), _ptr(out_vals), _ptr(out_found),
-                                    absent, _stream(stream)))
+    ov, of = _outs(out_vals, out_found, q.numel(), lambda: m.vbytes)
+    _check(lib().fks_sortmap_lookup(m.handle, _ptr(q, "q", 8), q.numel(), ov, of, absent, _stream(stream)))
 
 
 def fks_sortmap_export(m: SortMap, stream=None):

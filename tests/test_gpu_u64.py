@@ -256,6 +256,31 @@ def test_invalid_arguments(F):
                         F.make_opts(bound_factor=65))
 
 
+def test_binding_refuses_mismatched_buffers(F):
+    """Buffers the C ABI would misread are refused by the binding before any
+    launch: 32-bit keys, an int64 result buffer for an int32 map, a strided
+    needle view, a short flag buffer.  The map answers correctly afterwards."""
+    import torch
+    n = 2000
+    w = W.u64_workload(n, 500, 0.5, seed=21)
+    vals = np.arange(n, dtype=np.int32)
+    with pytest.raises(TypeError, match="keys"):
+        F.fks_build_u64(dev(w.keys.astype(np.int32)), dev(vals), 4)
+    gm = F.fks_build_u64(u64(w.keys), dev(vals), 4)
+    qt = u64(w.queries)
+    with pytest.raises(TypeError, match="out_vals"):
+        F.fks_lookup_u64(gm, qt, torch.empty(500, dtype=torch.int64, device="cuda"), None)
+    with pytest.raises(ValueError, match="contiguous"):
+        F.fks_lookup_u64(gm, u64(np.repeat(w.queries, 2))[::2], None,
+                         torch.empty(500, dtype=torch.uint8, device="cuda"))
+    with pytest.raises(ValueError, match="out_found"):
+        F.fks_lookup_u64(gm, qt, None, torch.empty(499, dtype=torch.uint8, device="cuda"))
+    out, found = gpu_lookup(F, gm, w.queries, i64=False)
+    om = O.build_u64(w.keys, vals.astype(np.int64), seed=4)
+    oo, of = O.lookup_u64(om, w.queries)
+    assert np.array_equal(out, oo) and np.array_equal(found, of)
+
+
 def test_full_size_2e26_keys_bit_exact(F):
     """2^26 keys, 2^26 queries at 90 % hits, the benchmark's launch
     configuration: whole tables and every lookup output against the oracle."""
