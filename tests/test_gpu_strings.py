@@ -186,3 +186,37 @@ def test_strings_up_to_the_per_lane_limit(F):
         assert_same(F, gm, om)
         out, found = gpu_lookup(F, gm, body, offs)
         assert found.all() and np.array_equal(out, vals)
+
+
+def test_longest_string_and_size_limits(F):
+    """The longest key a map takes (2^24 - 1 bytes) builds with the oracle's
+    table and is found; a key one byte longer is refused
+    (FKS_ERR_INVALID_ARG), a needle that long is absent without an error, and
+    n = 2^30 keys is refused before any device work."""
+    import ctypes
+    rng = np.random.default_rng(51)
+    big = 1 << 24
+    lens = np.array([big - 1, 5, 17, 0, 64])
+    offs = np.zeros(lens.size + 1, np.int64)
+    offs[1:] = np.cumsum(lens)
+    ctx = rng.integers(0, 256, int(offs[-1]), dtype=np.uint8)
+    vals = np.arange(lens.size)
+    om = O.build_bytes(ctx, offs, vals, seed=2)
+    assert om.status == O.OK
+    gm = gpu_build(F, ctx, offs, vals, 2)
+    assert_same(F, gm, om)
+    out, found = gpu_lookup(F, gm, ctx, offs)
+    assert found.all() and np.array_equal(out, vals)
+    needle = np.concatenate([ctx[:big - 1], np.array([7], np.uint8)])  # 2^24 bytes
+    out, found = gpu_lookup(F, gm, needle, [0, big])
+    assert found.tolist() == [0] and out.tolist() == [-1]
+    offs2 = np.array([0, big, big + 5], np.int64)
+    ctx2 = rng.integers(0, 256, big + 5, dtype=np.uint8)
+    with pytest.raises(F.FksError) as e:
+        gpu_build(F, ctx2, offs2, np.arange(2), 2)
+    assert e.value.status == F.FKS_ERR_INVALID_ARG
+    k = dev(np.zeros(8, np.int64))
+    h = ctypes.c_void_p()
+    st = F.lib().fks_build_u64(ctypes.c_void_p(k.data_ptr()), ctypes.c_void_p(k.data_ptr()), F.FKS_VAL_I64, 1 << 30,
+                               1, None, None, None, ctypes.byref(h))
+    assert st == F.FKS_ERR_INVALID_ARG and not h.value
