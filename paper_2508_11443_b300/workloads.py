@@ -547,3 +547,26 @@ def ctypes_sizeof_request() -> int:
 
     from . import fks as F
     return ctypes.sizeof(F.fks_request)
+
+
+STRUCTURED_KINDS = ("consecutive", "high_half", "both_halves", "bits", "top")
+
+
+def structured_keys(kind: str, n: int) -> np.ndarray:
+    """Distinct uint64 key sets with structure that a hash of the two 32-bit
+    halves must still spread: consecutive integers 0..n-1; i << 32 (equal low
+    halves); i * (2^32 + 1) (equal halves); the 64 single-bit keys, their
+    complements and zero (n ignored); 2^64 - 1 - i (the top of the range)."""
+    i = np.arange(n, dtype=np.uint64)
+    if kind == "consecutive":
+        return i
+    if kind == "high_half":
+        return i << np.uint64(32)
+    if kind == "both_halves":
+        return i * np.uint64(2**32 + 1)
+    if kind == "bits":
+        b = np.uint64(1) << np.arange(64, dtype=np.uint64)
+        return np.concatenate([b, ~b, np.zeros(1, np.uint64)])
+    if kind == "top":
+        return np.uint64(2**64 - 1) - i
+    raise ValueError(f"unknown key set {kind}")

@@ -256,6 +256,23 @@ def test_invalid_arguments(F):
                         F.make_opts(bound_factor=65))
 
 
+@pytest.mark.parametrize("kind", W.STRUCTURED_KINDS)
+def test_structured_key_sets_bit_exact(F, kind):
+    """Consecutive integers, keys equal in one or both 32-bit halves, single
+    bits and complements, the top of the range: tables and lookups equal the
+    oracle's."""
+    keys = W.structured_keys(kind, 5000)
+    vals = np.arange(keys.size, dtype=np.int64) * 3 - 5
+    om = O.build_u64(keys, vals, seed=23)
+    assert om.status == O.OK
+    gm = gpu_build(F, keys, vals, 23)
+    assert_same_tables(F, gm, om)
+    q = np.concatenate([keys, np.setdiff1d(W.structured_keys(kind, 9000), keys)[:2000]])
+    out, found = gpu_lookup(F, gm, q)
+    oo, of = O.lookup_u64(om, q)
+    assert np.array_equal(out, oo) and np.array_equal(found, of)
+
+
 def test_binding_refuses_mismatched_buffers(F):
     """Buffers the C ABI would misread are refused by the binding before any
     launch: 32-bit keys, an int64 result buffer for an int32 map, a strided

@@ -232,6 +232,22 @@ def test_build_invariants(n):
     assert np.array_equal(out, np.where(w.expect_found == 1, w.expect_vals, -7))
 
 
+STRUCTURED = list(W.STRUCTURED_KINDS)
+
+
+@pytest.mark.parametrize("kind", STRUCTURED)
+def test_structured_key_sets(kind):
+    keys = W.structured_keys(kind, 4096)
+    vals = np.arange(keys.size, dtype=np.int64) * 3 - 5
+    m = O.build_u64(keys, vals, seed=19)
+    assert m.status == O.OK and m.S <= 4 * keys.size
+    check_table(m, keys, vals)
+    others = np.setdiff1d(W.structured_keys(kind, 8192), keys)[:1000]
+    out, found = O.lookup_u64(m, np.concatenate([keys, others]), absent=-9)
+    assert found[: keys.size].all() and not found[keys.size:].any()
+    assert np.array_equal(out[: keys.size], vals) and (out[keys.size:] == -9).all()
+
+
 def test_n1_special_case():
     m = O.build_u64([123456789], [5], seed=1)
     assert m.S == 1 and m.desc[0] == np.uint64(1 << 32)
