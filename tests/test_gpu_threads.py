@@ -77,3 +77,69 @@ def test_concurrent_async_builds(F):
         d, s, _ = F.fks_map_export(m)
         om = O.build_u64(w.keys, w.vals, seed=9)
         assert np.array_equal(d, om.desc) and np.array_equal(s, om.slots)
+
+
+FIRST_USE = r"""
+import sys, threading
+import numpy as np
+import torch
+sys.path.insert(0, sys.argv[1])
+import oracle as O
+from paper_2508_11443_b300 import fks as F, workloads as W
+
+torch.cuda.set_device(0)
+torch.zeros(1, device="cuda")
+# u64 maps above and below the two-level grouping size, and string maps: the
+# first calls into the library in this process, from four threads at once
+cases = [("u", W.u64_workload((1 << 20) + 5, 1, 1.0, seed=31), 3), ("u", W.u64_workload(40000, 1, 1.0, seed=32), 4),
+         ("s", W.string_workload(1 << 20, 1, 1.0, seed=33), 5), ("s", W.string_workload(30000, 1, 1.0, seed=34), 6)]
+barrier = threading.Barrier(len(cases))
+got, errors = [None] * len(cases), []
+
+def run(i):
+    try:
+        kind, w, seed = cases[i]
+        torch.cuda.set_device(0)
+        s = torch.cuda.Stream()
+        with torch.cuda.stream(s):
+            if kind == "u":
+                k = torch.from_numpy(w.keys.view(np.int64)).cuda()
+                v = torch.from_numpy(w.vals).cuda()
+                s.synchronize()
+                barrier.wait()
+                m = F.fks_build_u64(k, v, seed)
+            else:
+                c, o = torch.from_numpy(w.ctx).cuda(), torch.from_numpy(w.offs).cuda()
+                v = torch.from_numpy(w.vals).cuda()
+                s.synchronize()
+                barrier.wait()
+                m = F.fks_build_bytes(c, o, v, seed)
+            got[i] = F.fks_map_export(m)[:2]
+    except Exception as e:  # reported by the parent
+        errors.append(repr(e))
+
+ts = [threading.Thread(target=run, args=(i,)) for i in range(len(cases))]
+for t in ts:
+    t.start()
+for t in ts:
+    t.join()
+assert not errors, errors
+for (kind, w, seed), (d, sl) in zip(cases, got):
+    om = O.build_u64(w.keys, w.vals, seed=seed) if kind == "u" else O.build_bytes(w.ctx, w.offs, w.vals, seed=seed)
+    assert np.array_equal(d, om.desc) and np.array_equal(sl, om.slots), kind
+print("first use ok")
+"""
+
+
+def test_concurrent_first_use_in_a_fresh_process(F):
+    """The library's one-time set-up (kernel attributes, occupancy, the SM
+    count) happens under concurrent first calls: four threads of a fresh
+    process start their builds together as the process's first calls into
+    the library, and every table equals the oracle's."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", FIRST_USE, root], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-4000:]
+    assert "first use ok" in r.stdout
