@@ -468,6 +468,34 @@ def run_bucket_variants(F, torch, hbm, keys, vals, queries, out, found, w, n, nq
     return res
 
 
+def run_inline_singletons(F, torch, hbm, keys, vals, queries, out, found, w, n, nq):
+    """The inline-singleton records (build option inline_singletons) on the
+    headline workload: the paper's tables plus a 16-byte record per bucket, so
+    a needle whose bucket holds no key or one key is answered by one random
+    access.  Byte model (32-byte sectors, a Poisson(1) bucket-size law): needle
+    8 + record sector + a slot sector for hits in buckets of two or more keys
+    (1 - 1/e of the hits) and misses that land in such a bucket (1 - 2/e) +
+    value 8 + flag 1."""
+    stream = torch.cuda.current_stream()
+    o = F.make_opts(inline_singletons=1)
+    bms = _timed(torch, stream, lambda: F.fks_build_u64(keys, vals, SEED, o))
+    m = F.fks_build_u64(keys, vals, SEED, o)
+    lms = _timed(torch, stream, lambda: F.fks_lookup_u64(m, queries, out, found, -1))
+    ok = np.array_equal(found.cpu().numpy(), w.expect_found) and \
+        np.array_equal(out.cpu().numpy(), np.where(w.expect_found == 1, w.expect_vals, -1))
+    info = F.fks_map_info(m)
+    e1 = float(np.exp(-1.0))
+    lq = 8 + SECTOR + SECTOR * (HIT * (1 - e1) + (1 - HIT) * (1 - 2 * e1)) + 8 + 1
+    del m
+    torch.cuda.empty_cache()
+    return {"workload": "the headline workload, map built with inline-singleton records",
+            "build_ms": bms, "lookup_ms": lms, "step_ms": bms + lms,
+            "map_bytes_per_key": info.bytes / n, "build_keys_per_s": n / (bms / 1e3),
+            "lookups_per_s": nq / (lms / 1e3), "keys_plus_lookups_per_s": (n + nq) / ((bms + lms) / 1e3),
+            "lookup_bytes_model": f"{lq:.2f} B/query", "lookup_GBps": lq * nq / (lms / 1e3) / 1e9,
+            "lookup_frac": lq * nq / (lms / 1e3) / 1e9 / hbm, "results_match_truth": bool(ok)}
+
+
 def run_from_array(F, W, torch, hbm, shift=0):
     """from_array (opts.dedup = 1): 2^26 pairs whose keys are drawn with
     replacement from 2^25 distinct keys (about 2.9e7 distinct); the first
@@ -860,6 +888,7 @@ def main():
     if not args.no_extras:
         line["bucket_variants"] = run_bucket_variants(F, torch, hbm, keys, vals, queries, out, found, w, n, nq,
                                                       tune=not (args.no_autotune or args.tuning))
+        line["inline_singletons"] = run_inline_singletons(F, torch, hbm, keys, vals, queries, out, found, w, n, nq)
         xs = args.extras_shift
         line["strings"] = run_strings(F, W, torch, hbm, xs)
         line["batched"] = run_batched(F, W, torch, hbm, xs)

@@ -85,6 +85,18 @@ typedef struct {
  * are 32-bit descriptor fields); larger builds return FKS_ERR_INVALID_ARG.
  * A struct_size that ends before keys_per_bucket is accepted (lambda 1).
  *
+ * inline_singletons = 1 (uint64 keys, lambda 1, fks_build_u64 and its
+ * _async / _host forms only; other builds return FKS_ERR_INVALID_ARG) adds a
+ * record array of 16 bytes per level-one bucket next to the unchanged
+ * tables: a bucket of one key holds {key, value}, any other bucket {x,
+ * desc[b]} with x a key that hashes to another bucket (0, or for the one
+ * bucket g(0) the least x >= 1 with g(x) != g(0)).  fks_lookup_u64 then reads
+ * the record first, and only needles of buckets with two or more keys go on
+ * to a slot: about 37 % of a map's keys sit alone in their bucket, whose
+ * lookups take one random access instead of the paper's two (Sec. 5).  The
+ * map holds 16 more bytes per bucket (fks_map_info: inline_singletons = 1;
+ * fks_map_export_records copies the records).
+ *
  * dedup = 1 turns a build into the paper's from_array (Sec. 3.2): the input
  * may hold equal keys (equal words, or equal byte strings), and the first
  * occurrence in input order wins -- per map for fks_build_batched.  The map
@@ -99,6 +111,7 @@ typedef struct {
   uint32_t spin_limit;       /* bound of every device wait, in polls (1<<20)     */
   uint32_t keys_per_bucket;  /* lambda: 1 (the paper), 2, 4, 8 or 16 (1)        */
   uint32_t dedup;            /* 1: from_array -- duplicate keys allowed (0)     */
+  uint32_t inline_singletons; /* 1: inline-singleton records (0)               */
 } fks_build_opts;
 
 typedef struct {
@@ -118,7 +131,7 @@ typedef struct {
   uint64_t nonempty_buckets;    /* buckets with s > 0                      */
   uint64_t buckets;             /* level-one buckets nb = descriptors      */
   uint32_t keys_per_bucket;     /* lambda of the build                     */
-  uint32_t reserved;
+  uint32_t inline_singletons;   /* 1: the map has inline-singleton records */
 } fks_map_info_t;
 
 /* Phase timings of the last build on the calling thread (CUDA events on the
@@ -539,6 +552,12 @@ fks_status fks_map_info(fks_map_t map, fks_map_info_t* h_out);
  * Any pointer may be NULL. */
 fks_status fks_map_export(fks_map_t map, uint64_t* h_desc, void* h_slots, uint8_t* h_ctx,
                           fks_stream_t stream);
+
+/* fks_map_export_records -- copy a map's inline-singleton records to host
+ * memory (synchronises `stream`): h_rec uint64[2 * buckets], bucket b at
+ * h_rec[2b], h_rec[2b + 1] as described at fks_build_opts.  A map built
+ * without the option: FKS_ERR_INVALID_ARG. */
+fks_status fks_map_export_records(fks_map_t map, uint64_t* h_rec, fks_stream_t stream);
 
 /* fks_map_import -- a map from tables that fks_map_export wrote (checkpoint /
  * resume: export, store the buffers and the info anywhere, import in another

@@ -6,8 +6,10 @@ the two share no code: ``fks_oracle.c`` is an independent, plain,
 single-threaded C restatement of the paper's functional construction
 (``make_1`` / ``make_2``, Sec. 2.3) and of the membership test (Sec. 2.2).
 
-This module only compiles that file with gcc (in-tree) and marshals numpy
-arrays through ctypes.
+This module compiles that file with gcc (in-tree) and marshals numpy arrays
+through ctypes.  It also writes out, in numpy and plain Python, the
+inline-singleton records of a built uint64 map and the lookup that reads
+them: a transform of the map's own tables, not a second construction.
 """
 from __future__ import annotations
 
@@ -318,6 +320,55 @@ def binary_search(sorted_keys, q: int) -> int:
 
 
 # ------------------------------------------------------------- table reading
+# ------------------------------------------------------------- inline-singleton records
+def inline_records(m: Map) -> np.ndarray:
+    """The inline-singleton records of a uint64 map (lambda 1), uint64[nb, 2],
+    written out from the map's own tables.  Bucket b with one key holds
+    {key, value}, the contents of its only slot.  Any other bucket holds
+    {x_b, desc[b]}, where x_b is a key of another bucket: 0, except for
+    b = g(0), where x_b is the least x >= 1 with g(x) != g(0); g(k) =
+    reduce(hash32(c1, k), nb) is the level-one hash of the final round."""
+    assert m.kind == "u64" and m.keys_per_bucket == 1 and m.status == OK
+    off, s, _ = desc_fields(m.desc)
+    g0 = reduce(hash32(m.c1, 0), m.nb)
+    x1 = 1
+    while m.nb > 1 and x1 < (1 << 16) and reduce(hash32(m.c1, x1), m.nb) == g0:
+        x1 += 1
+    rec = np.zeros((m.nb, 2), np.uint64)
+    rec[g0, 0] = x1
+    rec[:, 1] = m.desc
+    one = s == 1
+    rec[one, 0] = m.slots[off[one], 0]
+    rec[one, 1] = m.slots[off[one], 1]
+    return rec
+
+
+def lookup_u64_inline(m: Map, rec: np.ndarray, queries, absent: int = -1):
+    """Lookups that read the needle's record first, one needle at a time
+    (plain Python, for small inputs).  b = g(q) and {x, y} = rec[b].  If x = q,
+    q is the bucket's one key and y its value.  Else, if g(x) = b, the bucket
+    holds one other key: q is absent.  Else y is desc[b] and the lookup is the
+    paper's (Sec. 2.2): s = 0 means absent; otherwise the slot off + Hash c2 q
+    mod s^2 holds q or q is absent."""
+    out = np.full(len(queries), absent, np.int64)
+    found = np.zeros(len(queries), np.uint8)
+    for i, q in enumerate(np.asarray(queries, np.uint64).tolist()):
+        b = reduce(hash32(m.c1, q), m.nb)
+        x, y = int(rec[b, 0]), int(rec[b, 1])
+        if x == q:
+            out[i], found[i] = np.uint64(y).view(np.int64), 1
+            continue
+        if reduce(hash32(m.c1, x), m.nb) == b:
+            continue
+        off, s, att = y & 0xFFFFFFFF, (y >> 32) & 0xFFFFF, y >> 52
+        if s == 0:
+            continue
+        j = off + reduce(hash32(derive(m.seed, m.round, b, att), q), s * s)
+        if int(m.slots[j, 0]) == q:
+            out[i], found[i] = m.slots[j, 1].view(np.int64), 1
+    return out, found
+
+
 def desc_fields(desc: np.ndarray):
     """(slot_off, s, attempt) arrays of a descriptor array."""
     d = np.asarray(desc, np.uint64)

@@ -198,6 +198,7 @@ struct fks_map {
   uint64_t fpb = 0;
   uint64_t* desc = nullptr;
   uint64_t* slots = nullptr;
+  uint64_t* rec = nullptr;  // inline-singleton records, or null
   uint8_t* ctx = nullptr;
   // ownership (null for maps borrowed from a set)
   void* block = nullptr;
@@ -260,6 +261,7 @@ struct Opts {
   uint32_t bound = 4, attempt_cap = 4095, round_cap = 32, reject = 0, spin = 1u << 20, hold = 0;
   uint32_t lambda = 1;  // keys per level-one bucket
   uint32_t dedup = 0;   // from_array: first occurrence of equal keys wins
+  uint32_t inline1 = 0; // inline-singleton records (one-map u64 builds at lambda 1)
 };
 
 // Options of the older, shorter layout (without keys_per_bucket) are accepted.
@@ -272,8 +274,13 @@ static bool read_opts(const fks_build_opts* o, Opts* out) {
     if (o->dedup > 1) return false;
     out->dedup = o->dedup;
   }
+  if (o->struct_size >= offsetof(fks_build_opts, inline_singletons) + sizeof(uint32_t)) {
+    if (o->inline_singletons > 1) return false;
+    out->inline1 = o->inline_singletons;
+  }
   if (out->lambda != 1 && out->lambda != 2 && out->lambda != 4 && out->lambda != 8 && out->lambda != 16)
     return false;
+  if (out->inline1 && out->lambda != 1) return false;
   out->bound = 2 * (1 + out->lambda);  // E[sum s^2] < (1 + lambda) n: bound = twice that
   if (o->bound_factor) out->bound = o->bound_factor;
   if (o->attempt_cap) out->attempt_cap = o->attempt_cap;
@@ -310,6 +317,7 @@ struct BuildIn {
 struct SetMem {
   uint64_t* desc = nullptr;
   uint64_t* slots = nullptr;
+  uint64_t* rec = nullptr;  // inline-singleton records (2 words per bucket), or null
   uint8_t* ctx = nullptr;
   std::vector<uint64_t> slot_base;  // per map
   std::vector<uint64_t> desc_base;  // per map
@@ -433,12 +441,15 @@ fks_status SetBuild::init(const BuildIn& in_, const Opts& o_, const Alloc& A_, c
   const size_t o_desc = cm.take<uint64_t>(desc_total);
   const size_t o_slots = cm.take<uint64_t>(slot_total * W);
   const size_t o_ctx = cm.take<uint8_t>(str ? ctx_bytes + 16 : 0);
+  const bool with_rec = o.inline1 && !str && m == 1;
+  const size_t o_rec = cm.take<uint64_t>(with_rec ? 2 * desc_total : 0);
   block = static_cast<uint8_t*>(A.get(cm.off, st));
   if (!block) return fail(FKS_ERR_OUT_OF_MEMORY, "allocation of map tables failed");
   block_bytes = cm.off;
   mem.desc = reinterpret_cast<uint64_t*>(block + o_desc);
   mem.slots = reinterpret_cast<uint64_t*>(block + o_slots);
   mem.ctx = str ? block + o_ctx : nullptr;
+  mem.rec = with_rec ? reinterpret_cast<uint64_t*>(block + o_rec) : nullptr;
   mem.slot_base = slot_base;
   mem.desc_base = desc_base;
   // scratch for the largest pass (the first one holds every map)
@@ -505,6 +516,7 @@ fks_status SetBuild::init(const BuildIn& in_, const Opts& o_, const Alloc& A_, c
   p.ctx = mem.ctx;
   p.desc = mem.desc;
   p.slots = mem.slots;
+  p.rec = mem.rec;
   p.logB = logB;
   p.cfg.attempt_cap = o.attempt_cap;
   p.cfg.reject = o.reject;
@@ -540,6 +552,12 @@ uint32_t SetBuild::fill_tables(const std::vector<uint32_t>& active, uint8_t* up)
     M.nb = uint32_t(nbs[j]);
     M.slot_cap = uint32_t(uint64_t(o.bound) * n);
     M.part_begin = pp;
+    if (mem.rec) {  // this round's key for the descriptor record of bucket g(0)
+      p.rec_g0 = reduce32(hash32(M.c1, 0), M.nb);
+      uint64_t x = 1;
+      while (M.nb > 1 && x < (1u << 16) && reduce32(hash32(M.c1, x), M.nb) == p.rec_g0) ++x;
+      p.rec_x1 = x;
+    }
     h_pseg[a] = pe;
     h_qseg[a] = pp;
     pe += n;
@@ -710,9 +728,10 @@ fks_status SetBuild::run(cudaStream_t st, GraphPass* g) {
       M.lambda = o.lambda;
       M.desc = mem.desc + mem.desc_base[j];
       M.slots = mem.slots + mem.slot_base[j] * W;
+      M.rec = mem.rec;
       M.ctx = mem.ctx;
       M.ctx_bytes = ctx_bytes;
-      M.bytes = sizeof(uint64_t) * (M.nb + W * M.slot_cap);
+      M.bytes = sizeof(uint64_t) * (M.nb * (mem.rec ? 3 : 1) + W * M.slot_cap);
     }
     active.swap(next);
   }
@@ -878,6 +897,8 @@ static fks_status build_single(const BuildIn& in, const fks_build_opts* opts,
   NvtxRange range("fks_build");
   Opts o;
   if (!read_opts(opts, &o)) return fail(FKS_ERR_INVALID_ARG, "bad build options");
+  if (o.inline1 && in.kind != FKS_KEY_U64)
+    return fail(FKS_ERR_INVALID_ARG, "inline_singletons: uint64 keys only");
   Alloc A(alloc);
   void* block = nullptr;
   size_t bb = 0;
@@ -1128,6 +1149,11 @@ fks_status fks_lookup_u64(fks_map_t map, const uint64_t* q, uint64_t nq, void* o
   if (map->kind != FKS_KEY_U64) return fail(FKS_ERR_INVALID_ARG, "fks_lookup_u64: not a u64 map");
   if (nq == 0) return FKS_OK;
   if (!q || !absent_fits(map, absent)) return fail(FKS_ERR_INVALID_ARG, "fks_lookup_u64: bad arguments");
+  if (map->rec) {
+    FKS_CUDA(launch_lookup_inline(lookup_view(*map), map->rec, q, nq, out_vals, map->vt == FKS_VAL_I64, out_found,
+                                  absent, sm_count(), reinterpret_cast<cudaStream_t>(stream)));
+    return FKS_OK;
+  }
   FKS_CUDA(launch_lookup_u64(lookup_view(*map), q, nq, out_vals, map->vt == FKS_VAL_I64, out_found,
                              absent, sm_count(), lookup_shape_for(map->lambda), reinterpret_cast<cudaStream_t>(stream)));
   return FKS_OK;
@@ -1164,6 +1190,7 @@ fks_status fks_build_batched(fks_key_kind kind, const uint64_t* keys, const uint
   h_seg = seg_copy.data();
   Opts o;
   if (!read_opts(opts, &o)) return fail(FKS_ERR_INVALID_ARG, "bad build options");
+  if (o.inline1) return fail(FKS_ERR_INVALID_ARG, "fks_build_batched: inline_singletons is for one-map builds");
   Alloc A(alloc);
   const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   BuildIn in{kind, keys, ctx, offs, vals, val_type, m, h_seg, h_seeds};
@@ -1242,6 +1269,7 @@ fks_status fks_build_graph_create(fks_key_kind kind, const uint64_t* keys, const
   Opts o;
   if (!read_opts(opts, &o)) return fail(FKS_ERR_INVALID_ARG, "bad build options");
   if (o.dedup) return fail(FKS_ERR_INVALID_ARG, "fks_build_graph_create: dedup changes the sizes; not recordable");
+  if (o.inline1) return fail(FKS_ERR_INVALID_ARG, "fks_build_graph_create: inline_singletons is for one-map builds");
   const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   sm_count();
   fks_build_graph* g = new fks_build_graph();
@@ -1359,6 +1387,17 @@ fks_status fks_map_info(fks_map_t map, fks_map_info_t* h_out) {
   h_out->nonempty_buckets = map->nonempty;
   h_out->buckets = map->nb;
   h_out->keys_per_bucket = map->lambda;
+  h_out->inline_singletons = map->rec ? 1u : 0u;
+  return FKS_OK;
+}
+
+fks_status fks_map_export_records(fks_map_t map, uint64_t* h_rec, fks_stream_t stream) {
+  if (!map || !h_rec) return fail(FKS_ERR_INVALID_ARG, "fks_map_export_records: NULL argument");
+  if (const fks_status bs = settle(map)) return bs;
+  if (!map->rec) return fail(FKS_ERR_INVALID_ARG, "fks_map_export_records: the map has no inline records");
+  const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  FKS_CUDA(cudaMemcpyAsync(h_rec, map->rec, 2 * sizeof(uint64_t) * map->nb, cudaMemcpyDeviceToHost, st));
+  FKS_CUDA(cudaStreamSynchronize(st));
   return FKS_OK;
 }
 

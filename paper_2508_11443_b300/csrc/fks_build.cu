@@ -940,7 +940,15 @@ __device__ void write_partition(const PassDev& p, const MapRegs& M, uint32_t b0,
   const uint32_t t = threadIdx.x;
   for (uint32_t lb = t; lb < nb; lb += kPartThreads) {
     const uint32_t s = gst[lb + 1] - gst[lb];
-    p.desc[M.desc_base + b0 + lb] = desc_pack(uint32_t(excl + soff[lb]), s, att[lb]);
+    const uint64_t d = desc_pack(uint32_t(excl + soff[lb]), s, att[lb]);
+    p.desc[M.desc_base + b0 + lb] = d;
+    if (PW == 1 && p.rec) {  // inline-singleton record of the bucket
+      const uint32_t b = b0 + lb;
+      ulonglong2 r;
+      r.x = s == 1 ? gkey[gst[lb]] : (b == p.rec_g0 ? p.rec_x1 : 0ull);
+      r.y = s == 1 ? gpay[gst[lb]] : d;
+      reinterpret_cast<ulonglong2*>(p.rec)[M.desc_base + b] = r;
+    }
   }
   if (owner_mode) {
     const uint64_t slot_part = M.slot_base + excl;

@@ -113,6 +113,13 @@ struct PassDev {
   // outputs
   uint64_t* desc;             // descriptor array of the set
   uint64_t* slots;            // slot array of the set (2 or 4 words per slot)
+  // Inline-singleton records (one-map u64 passes with the option, else null):
+  // rec[2b .. 2b+1] = {key, value} of a one-key bucket b, else {a key that
+  // does not hash to b, desc[b]}.  That key is 0 except in bucket rec_g0 =
+  // g(0), where it is rec_x1 (the least x >= 1 with g(x) != g(0)).
+  uint64_t* rec;
+  uint64_t rec_x1;
+  uint32_t rec_g0;
   BuildCfg cfg;
 };
 
@@ -233,6 +240,9 @@ struct LookupMap {
 cudaError_t launch_lookup_u64(const LookupMap& M, const uint64_t* q, uint64_t nq, void* out,
                               int out_i64, uint8_t* found, int64_t absent, int sms,
                               const LookupShape& shape, cudaStream_t stream);
+// Lookups of a map with inline-singleton records (rec: 2 words per bucket).
+cudaError_t launch_lookup_inline(const LookupMap& M, const uint64_t* rec, const uint64_t* q, uint64_t nq, void* out,
+                                 int out_i64, uint8_t* found, int64_t absent, int sms, cudaStream_t stream);
 cudaError_t launch_lookup_bytes(const LookupMap& M, const uint8_t* qctx, const int64_t* qoffs,
                                 uint64_t nq, void* out, int out_i64, uint8_t* found,
                                 int64_t absent, int sms, cudaStream_t stream);

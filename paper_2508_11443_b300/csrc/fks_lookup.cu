@@ -56,6 +56,89 @@ __device__ __forceinline__ ulonglong4_32a ld_na_u256(const uint64_t* p, uint64_t
   return v;
 }
 
+// Lookups through inline-singleton records: one 16-byte probe of rec[b]
+// answers every needle whose bucket holds no key or one key (hit or miss);
+// only the others go on to their slot, as in k_lookup_u64.  A record {x, y}
+// is a one-key bucket's {key, value} exactly when x hashes to b; otherwise y
+// is desc[b] (and x, hashing elsewhere, equals no needle of bucket b).
+template <bool kI64>
+__global__ void __launch_bounds__(512) k_lookup_inline(LookupMap M, const uint64_t* __restrict__ rec,
+                                                       const uint64_t* __restrict__ q, uint64_t nq,
+                                                       void* __restrict__ out, uint8_t* __restrict__ found,
+                                                       int64_t absent, int vec) {
+  constexpr int kQ = 4;
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x * kQ;
+  const uint64_t keep = policy_keep(), strm = policy_stream();
+  for (uint64_t base = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) * kQ; base < nq; base += stride) {
+    const bool full = vec && base + kQ <= nq;
+    uint64_t k[kQ];
+    if (full) {
+#pragma unroll
+      for (int i = 0; i < kQ; i += 2) {
+        const ulonglong2 v = __ldcs(reinterpret_cast<const ulonglong2*>(q + base + i));
+        k[i] = v.x;
+        k[i + 1] = v.y;
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) k[i] = base + i < nq ? __ldcs(q + base + i) : 0;
+    }
+    uint32_t b[kQ];
+    ulonglong2 r[kQ];
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      b[i] = reduce32(hash32(M.c1, k[i]), M.nb);
+      r[i] = ld_na_u128(rec + 2ull * b[i], keep);
+    }
+    ulonglong2 sl[kQ];
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      sl[i] = make_ulonglong2(~k[i], 0);
+      if (r[i].x == k[i]) {
+        sl[i] = r[i];  // the bucket's one key
+      } else if (reduce32(hash32(M.c1, r[i].x), M.nb) != b[i]) {
+        const uint64_t d = r[i].y;  // a descriptor record
+        const uint32_t s = desc_s(d);
+        if (s) {
+          const HashConsts c = derive(M.seed, M.round, b[i], desc_attempt(d));
+          const uint32_t jj = desc_off(d) + reduce32(hash32(c, k[i]), s * s);
+          sl[i] = ld_na_u128(M.slots + 2ull * jj, strm);
+        }
+      }
+    }
+    int64_t v[kQ];
+    uint32_t f = 0;
+#pragma unroll
+    for (int i = 0; i < kQ; ++i) {
+      const bool hit = sl[i].x == k[i];
+      v[i] = hit ? int64_t(sl[i].y) : absent;
+      f |= uint32_t(hit) << (8 * i);
+    }
+    if (full) {
+      if (out) {
+        if (kI64) {
+          __stcs(reinterpret_cast<longlong2*>(static_cast<int64_t*>(out) + base), make_longlong2(v[0], v[1]));
+          __stcs(reinterpret_cast<longlong2*>(static_cast<int64_t*>(out) + base + 2), make_longlong2(v[2], v[3]));
+        } else {
+          __stcs(reinterpret_cast<int4*>(static_cast<int32_t*>(out) + base),
+                 make_int4(int(v[0]), int(v[1]), int(v[2]), int(v[3])));
+        }
+      }
+      if (found) __stcs(reinterpret_cast<unsigned int*>(found + base), f);
+    } else {
+#pragma unroll
+      for (int i = 0; i < kQ; ++i) {
+        if (base + i >= nq) break;
+        if (out) {
+          if (kI64) static_cast<int64_t*>(out)[base + i] = v[i];
+          else static_cast<int32_t*>(out)[base + i] = int32_t(v[i]);
+        }
+        if (found) found[base + i] = uint8_t((f >> (8 * i)) & 1u);
+      }
+    }
+  }
+}
+
 template <int kQ, bool kI64, int NT>
 __global__ void __launch_bounds__(NT) k_lookup_u64(LookupMap M, const uint64_t* __restrict__ q, uint64_t nq,
                                                    void* __restrict__ out, uint8_t* __restrict__ found,
@@ -374,6 +457,20 @@ static void lookup_u64_q(const LookupMap& M, const uint64_t* q, uint64_t nq, voi
   if (block == 128) lookup_u64_at<kQ, 128>(M, q, nq, out, out_i64, found, absent, vec, grid, stream);
   else if (block == 512) lookup_u64_at<kQ, 512>(M, q, nq, out, out_i64, found, absent, vec, grid, stream);
   else lookup_u64_at<kQ, 256>(M, q, nq, out, out_i64, found, absent, vec, grid, stream);
+}
+
+cudaError_t launch_lookup_inline(const LookupMap& M, const uint64_t* rec, const uint64_t* q, uint64_t nq, void* out,
+                                 int out_i64, uint8_t* found, int64_t absent, int sms, cudaStream_t stream) {
+  if (nq == 0) return cudaSuccess;
+  const int vec = ((reinterpret_cast<uintptr_t>(q) | reinterpret_cast<uintptr_t>(out) |
+                    reinterpret_cast<uintptr_t>(found)) & 15u) == 0;
+  uint64_t blocks = (nq + 4 * 512 - 1) / (4 * 512);
+  const uint64_t cap = uint64_t(sms) * 1024;
+  if (blocks > cap) blocks = cap;
+  if (out_i64) k_lookup_inline<true><<<unsigned(blocks), 512, 0, stream>>>(M, rec, q, nq, out, found, absent, vec);
+  else k_lookup_inline<false><<<unsigned(blocks), 512, 0, stream>>>(M, rec, q, nq, out, found, absent, vec);
+  note_launches(1);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_lookup_u64(const LookupMap& M, const uint64_t* q, uint64_t nq, void* out,

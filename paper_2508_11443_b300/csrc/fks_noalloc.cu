@@ -130,6 +130,9 @@ extern "C" fks_status fks_build_u64_noalloc(const uint64_t* keys, const void* va
     // the deduplicating pre-pass needs buffers of its own
     if (opts->struct_size >= offsetof(fks_build_opts, dedup) + sizeof(uint32_t) && opts->dedup)
       return noalloc_fail(FKS_ERR_INVALID_ARG, "fks_build_u64_noalloc: dedup is not available");
+    if (opts->struct_size >= offsetof(fks_build_opts, inline_singletons) + sizeof(uint32_t) &&
+        opts->inline_singletons)
+      return noalloc_fail(FKS_ERR_INVALID_ARG, "fks_build_u64_noalloc: inline_singletons is not available");
   }
   if (slot_capacity < uint64_t(bound) * n)
     return noalloc_fail(FKS_ERR_INVALID_ARG,

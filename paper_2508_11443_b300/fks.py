@@ -39,7 +39,8 @@ class fks_build_opts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_size_t), ("bound_factor", ctypes.c_uint32),
                 ("attempt_cap", ctypes.c_uint32), ("round_cap", ctypes.c_uint32),
                 ("reject_attempts", ctypes.c_uint32), ("spin_limit", ctypes.c_uint32),
-                ("keys_per_bucket", ctypes.c_uint32), ("dedup", ctypes.c_uint32)]
+                ("keys_per_bucket", ctypes.c_uint32), ("dedup", ctypes.c_uint32),
+                ("inline_singletons", ctypes.c_uint32)]
 
 
 class fks_map_info_t(ctypes.Structure):
@@ -50,7 +51,7 @@ class fks_map_info_t(ctypes.Structure):
                 ("max_attempt", ctypes.c_uint32), ("key_kind", ctypes.c_uint32),
                 ("val_type", ctypes.c_uint32), ("overflow_partitions", ctypes.c_uint32),
                 ("nonempty_buckets", ctypes.c_uint64), ("buckets", ctypes.c_uint64),
-                ("keys_per_bucket", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("keys_per_bucket", ctypes.c_uint32), ("inline_singletons", ctypes.c_uint32)]
 
 
 class fks_build_profile(ctypes.Structure):
@@ -608,6 +609,17 @@ def fks_map_export(m: Map, stream=None):
     if ctx is not None:
         ctx = ctx[: info.context_bytes]
     return desc, slots, ctx
+
+
+def fks_map_export_records(m: Map, stream=None) -> np.ndarray:
+    """The inline-singleton records, uint64[buckets, 2], on the host."""
+    info = fks_map_info(m)
+    rec = np.empty((info.buckets, 2), np.uint64)
+    L = lib()
+    L.fks_map_export_records.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.fks_map_export_records.restype = ctypes.c_int
+    _check(L.fks_map_export_records(m.handle, rec.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+    return rec
 
 
 def fks_map_import(info: fks_map_info_t, desc: np.ndarray, slots: np.ndarray, ctx=None, stream=None) -> Map:

@@ -605,3 +605,64 @@ def test_eytzinger_search_matches_binary_search():
             assert (k != 0) == (i >= 0)
             if k:
                 assert ek[k] == q and ev[k] == i
+
+
+# ------------------------------------------------------------------ inline-singleton records
+def level_one(m, xs):
+    c1 = [np.uint64(x) for x in O.derive(m.seed, m.round, O.TAG_L1, 0)]
+    return np_reduce(np_hash(c1, np.asarray(xs, np.uint64)), m.nb).astype(np.int64)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 1000, 20000])
+def test_inline_records_follow_their_definition(n):
+    """Checked key by key: the bucket of a key that is alone in it holds
+    {key, value}; every other bucket holds its own descriptor and a first word
+    that hashes to another bucket (so that no needle of the bucket equals it)."""
+    w = W.u64_workload(n, 1, 1.0, seed=n + 40)
+    m = O.build_u64(w.keys, w.vals, seed=41)
+    rec = O.inline_records(m)
+    _, s, _ = O.desc_fields(m.desc)
+    bk = level_one(m, w.keys)
+    one = s[bk] == 1
+    assert np.array_equal(rec[bk[one], 0], w.keys[one])
+    assert np.array_equal(rec[bk[one], 1].view(np.int64), w.vals[one])
+    other = np.nonzero(s != 1)[0]
+    assert np.array_equal(rec[other, 1], m.desc[other])
+    if m.nb > 1:
+        assert (level_one(m, rec[other, 0]) != other).all()
+    if n >= 20000:  # P(a key is alone in its bucket) = (1 - 1/n)^(n-1) ~ 1/e
+        assert abs(one.mean() - np.exp(-1)) < 0.01
+
+
+@pytest.mark.parametrize("kind", STRUCTURED + ["random"])
+def test_inline_lookup_equals_the_papers_lookup(kind):
+    """The record-first lookup answers exactly as the paper's two-probe
+    lookup and as a dictionary, members, non-members, 0 and 2^64 - 1."""
+    keys = W.key_stream(71, 1500) if kind == "random" else W.structured_keys(kind, 1500)
+    vals = np.arange(keys.size, dtype=np.int64) * 7 - 3000
+    m = O.build_u64(keys, vals, seed=73)
+    rec = O.inline_records(m)
+    extra = np.array([0, 2**64 - 1, 1, 2**63], np.uint64)
+    q = np.concatenate([keys, W.key_stream(72, 1500), extra])
+    oi, fi = O.lookup_u64_inline(m, rec, q, absent=-5)
+    op, fp = O.lookup_u64(m, q, absent=-5)
+    assert np.array_equal(oi, op) and np.array_equal(fi, fp)
+    d = dict(zip(keys.tolist(), vals.tolist()))
+    assert [int(f) for f in fi] == [int(x in d) for x in q.tolist()]
+    assert oi.tolist() == [d.get(x, -5) for x in q.tolist()]
+
+
+def test_inline_records_of_a_later_round():
+    """A map whose table comes from level-one round >= 1 (a tight space
+    bound): the records follow that round's hash."""
+    keys = W.key_stream(81, 3000)
+    for seed in range(200):
+        m = O.build_u64(keys, np.arange(3000), seed=seed, bound_factor=2)
+        if m.status == O.OK and m.round >= 1:
+            break
+    assert m.round >= 1
+    rec = O.inline_records(m)
+    q = np.concatenate([keys, W.key_stream(82, 500)])
+    oi, fi = O.lookup_u64_inline(m, rec, q)
+    op, fp = O.lookup_u64(m, q)
+    assert np.array_equal(oi, op) and np.array_equal(fi, fp)
