@@ -71,6 +71,16 @@ def load_traffic():
     return out
 
 
+def kernel_traffic(kernel: str, units: int):
+    """DRAM bytes of one launch over `units` keys or queries, scaled from the
+    committed 2^26 figure; None once the kernel's sources have changed since
+    the counters were taken."""
+    t = load_traffic()
+    if kernel in t and t[kernel][1] == kernel_digest(kernel):
+        return t[kernel][0] * units / float(1 << 26)
+    return None
+
+
 # source files each kernel is compiled from (digest ties ncu counters to code)
 KERNEL_SOURCES = {
     "k_lookup_u64": ["fks_device.cuh", "fks_internal.cuh", "fks_strings.cuh", "fks_lookup.cu"],
@@ -79,6 +89,7 @@ KERNEL_SOURCES = {
     "k_partition_count": ["fks_device.cuh", "fks_internal.cuh", "fks_strings.cuh", "fks_build.cu"],
     "k_scatterA": ["fks_device.cuh", "fks_internal.cuh", "fks_split.cu"],
     "k_scatterB": ["fks_device.cuh", "fks_internal.cuh", "fks_split.cu"],
+    "k_lookup_inline": ["fks_device.cuh", "fks_internal.cuh", "fks_strings.cuh", "fks_lookup.cu"],
 }
 
 
@@ -493,7 +504,8 @@ def run_inline_singletons(F, torch, hbm, keys, vals, queries, out, found, w, n, 
             "map_bytes_per_key": info.bytes / n, "build_keys_per_s": n / (bms / 1e3),
             "lookups_per_s": nq / (lms / 1e3), "keys_plus_lookups_per_s": (n + nq) / ((bms + lms) / 1e3),
             "lookup_bytes_model": f"{lq:.2f} B/query", "lookup_GBps": lq * nq / (lms / 1e3) / 1e9,
-            "lookup_frac": lq * nq / (lms / 1e3) / 1e9 / hbm, "results_match_truth": bool(ok)}
+            "lookup_frac": lq * nq / (lms / 1e3) / 1e9 / hbm, "results_match_truth": bool(ok),
+            "lookup_traffic": kernel_traffic("k_lookup_inline", nq)}
 
 
 def run_from_array(F, W, torch, hbm, shift=0):
@@ -809,10 +821,7 @@ def main():
         v["frac"] = v["GBps"] / hbm
     # the dominant single kernel carries the roofline object
     dom = max(("k_lookup_u64", "k_part_build"), key=lambda k: kernels[k]["ms"])
-    traffic = load_traffic()
-    tr = None
-    if dom in traffic and traffic[dom][1] == kernel_digest(dom):
-        tr = traffic[dom][0]
+    tr = kernel_traffic(dom, nq if dom == "k_lookup_u64" else n)
     D = kernels[dom]
     roofline = {"bound": "hbm", "achieved": D["GBps"], "peak": hbm, "unit": "GB/s",
                 "frac": D["frac"], "traffic": tr, "kernel": dom, "peak_source": peak_kind,
