@@ -572,8 +572,11 @@ fks_status fks_map_export_records(fks_map_t map, uint64_t* h_rec, fks_stream_t s
  * uploaded (every non-empty bucket's s^2 slots in order inside the slot
  * array, sum s = n, sum s^2 = slots); a mismatch returns FKS_ERR_INVALID_ARG.
  * The map answers lookups exactly as the exported one (the level-one and
- * fingerprint constants are re-derived from seed and round).  Blocks until
- * the upload is done; the handle is freed by fks_map_destroy. */
+ * fingerprint constants are re-derived from seed and round).  Inline-singleton
+ * records are not part of a checkpoint: a map exported with them is imported
+ * without (info.inline_singletons = 0) and answers through its descriptors
+ * and slots, with the same results.  Blocks until the upload is done; the
+ * handle is freed by fks_map_destroy. */
 fks_status fks_map_import(const fks_map_info_t* h_info, const uint64_t* h_desc, const void* h_slots,
                           const uint8_t* h_ctx, const fks_allocator* alloc, fks_stream_t stream, fks_map_t* out);
 

@@ -116,3 +116,21 @@ def test_refused_where_it_does_not_apply(F):
     assert F.fks_map_info(plain).inline_singletons == 0
     with pytest.raises(F.FksError):
         F.fks_map_export_records(plain)
+
+
+def test_checkpoint_of_a_map_with_records(F, tmp_path):
+    """A checkpoint holds the paper's tables only: the imported map has no
+    records and answers through its descriptors, with the same results."""
+    import torch
+    w = W.u64_workload(30000, 40000, 0.5, seed=95)
+    om, gm = check(F, w.keys, w.vals, 96, w.queries)
+    path = str(tmp_path / "inline_map.npz")
+    F.fks_map_save(gm, path)
+    back = F.fks_map_load(path)
+    assert F.fks_map_info(back).inline_singletons == 0
+    out = torch.empty(len(w.queries), dtype=torch.int64, device="cuda")
+    found = torch.empty(len(w.queries), dtype=torch.uint8, device="cuda")
+    F.fks_lookup_u64(back, dev(w.queries), out, found, -1)
+    torch.cuda.synchronize()
+    oo, of = O.lookup_u64(om, w.queries)
+    assert np.array_equal(found.cpu().numpy(), of) and np.array_equal(out.cpu().numpy(), oo)
